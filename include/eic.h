@@ -1,0 +1,182 @@
+/*
+ * libeic — single-source shortest paths on undirected graphs with positive
+ * integer weights by the EIC heuristic method of Yu, Wang and Luo, "A
+ * Heuristic Algorithm for Shortest Path Search" (arXiv 2506.19349), on one
+ * NVIDIA GB300 (sm_103a).
+ *
+ * Plain C ABI: no C++ or PyTorch types cross it. Every call returns an int
+ * status (EIC_OK or an EIC_E* code); no call aborts, traps or exits the
+ * process. Device pointers are CUDA global-memory addresses on the current
+ * device; host pointers are ordinary process memory. A "stream" argument is a
+ * cudaStream_t passed as void* (NULL = the legacy default stream).
+ *
+ * Distances are uint32 with +infinity = EIC_INF (0xFFFFFFFF), the paper's
+ * "+inf" for unreachable vertices (Section 2). Results are exact: dist[v] is
+ * lsp(s, v), the length of the shortest path, identical to Dijkstra's.
+ */
+#ifndef EIC_H
+#define EIC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define EIC_INF 0xFFFFFFFFu
+#define EIC_RATIO_NUM 4096 /* entries of the RtoW weight-quantile table (Section 4.1) */
+
+/* Status codes. */
+#define EIC_OK 0
+#define EIC_EINVAL 1    /* bad argument: NULL pointer, vertex id >= n, weight 0, size limit */
+#define EIC_ENOMEM 2    /* device or host allocation failed, or a fixed capacity was exceeded */
+#define EIC_ECUDA 3     /* a CUDA runtime call failed (no device, launch error, ...) */
+#define EIC_EOVERFLOW 4 /* the largest shortest distance plus the largest weight reaches 2^32-1 */
+#define EIC_ETIMEOUT 5  /* a bounded device-side wait (grid barrier) ran out; the context stays usable */
+#define EIC_EBUSY 6     /* the object is in use by another call */
+
+/* Opaque, device-resident graph owned by the library (create/destroy). */
+typedef struct eic_graph eic_graph;
+
+/* Tunable parameters. eic_params_default() fills the paper's settings
+ * (Section 4.1): alpha = 3, beta = 0.9, ST_NUM = 1024; RATIO_NUM is fixed at
+ * EIC_RATIO_NUM when the graph is created.
+ *   alpha, beta   Eq. 1-3 constants (beta in (0, 1)).
+ *   st_num        size of the Function 2 candidate grid (Section 4.1), >= 1.
+ *   gap_shift     step-width multiplier 2^gap_shift applied to Eq. 3's gap
+ *                 (0 = the paper; any value keeps distances exact).
+ *   block_threads threads per block of the relaxation kernel (0 = library
+ *                 choice; else a multiple of 32 in [128, 1024]).
+ *   heavy_min     window length above which a vertex's edges are spread over
+ *                 the whole grid instead of one warp (0 = library choice).
+ *   max_spin_log2 bound on each grid-barrier wait, 2^max_spin_log2 polls of
+ *                 about 100 ns (0 = library choice, about 2 s); exceeding it
+ *                 returns EIC_ETIMEOUT.
+ *   flags         EIC_FLAG_* bits. */
+typedef struct {
+  uint32_t alpha;
+  double beta;
+  uint32_t st_num;
+  uint32_t gap_shift;
+  uint32_t block_threads;
+  uint32_t heavy_min;
+  uint32_t max_spin_log2;
+  uint32_t flags;
+  uint32_t reserved[8];
+} eic_params;
+
+#define EIC_FLAG_NO_PULL 1u /* force st = lb (disable traversal optimisation; still exact) */
+
+/* Per-step trace row: the thresholds a step ran with and the statistics of
+ * Section 3 that produced them. */
+typedef struct {
+  int64_t lb, ub, st;  /* step window [lb, ub) and selection threshold st; step 1 reports its final ub */
+  int64_t gap_lb;      /* gap(lb) of Eq. 3 */
+  uint64_t sumd_lb;    /* sumD(lb): total degree of {v : lsp(s, v) >= lb} */
+  uint64_t highd_lb;   /* highD(lb) */
+  uint64_t rounds;     /* relaxation rounds (synchronisations) in the step */
+  uint64_t settled;    /* vertices whose distance fell in [lb, ub) */
+} eic_step;
+
+/* Counters of one query (Section 4: nSync, nFrontier, nTrav before
+ * normalisation). trace/trace_cap are inputs: when trace is a host array of
+ * trace_cap rows, up to trace_cap rows are written and trace_len reports the
+ * number of steps. */
+typedef struct {
+  uint64_t steps;
+  uint64_t rounds;     /* nSync */
+  uint64_t frontier;   /* vertices relaxed from (nFrontier, leaves excluded) */
+  uint64_t traversed;  /* nTrav: window entries relaxed plus pull requests */
+  uint64_t pulls;      /* pull requests (entries examined by Function 1's pull) */
+  uint64_t improved;   /* successful relaxations */
+  uint64_t heavy;      /* vertex windows spread over the grid */
+  eic_step* trace;
+  uint64_t trace_cap;
+  uint64_t trace_len;
+} eic_stats;
+
+/* Fill *p with the paper's defaults (Section 4.1). Returns EIC_EINVAL if p is NULL. */
+int eic_params_default(eic_params* p);
+
+/* Human-readable text for a status code (static storage, never NULL). */
+const char* eic_strerror(int status);
+
+/* Library version as major*10000 + minor*100 + patch. */
+int eic_version(void);
+
+/*
+ * Build a device graph from num_tuples raw undirected tuples (src[i], dst[i],
+ * w[i]) over vertices 0..num_vertices-1 (preprocessing of Section 4.1).
+ * Self-loops are dropped, a pair given several times keeps its smallest
+ * weight, every pair is stored in both directions, each vertex's neighbours
+ * are sorted by (weight, neighbour), and the weight quantile table RtoW and
+ * the degree statistics are computed on the device.
+ *   src, dst, w    arrays of num_tuples uint32; device pointers when
+ *                  ptrs_on_device != 0, else host pointers. Caller-owned,
+ *                  read only, copied; may be freed when the call returns.
+ *   num_vertices   n >= 1, n < 2^32 - 1.
+ *   stream         work is enqueued here; the call synchronises it before
+ *                  returning.
+ *   out            receives the new graph (NULL on failure).
+ * Errors: EIC_EINVAL (NULL pointer, endpoint >= n, weight 0, n out of
+ * range, num_tuples >= 2^31 directed entries per 2), EIC_ENOMEM, EIC_ECUDA.
+ */
+int eic_graph_create(const uint32_t* src, const uint32_t* dst, const uint32_t* w, uint64_t num_tuples,
+                     uint32_t num_vertices, int ptrs_on_device, void* stream, eic_graph** out);
+
+/* Graph facts: vertex count, undirected edge count m (after dedup), largest
+ * degree, largest and smallest weight, highD(0). Any output may be NULL. */
+int eic_graph_info(const eic_graph* g, uint32_t* n, uint64_t* m, uint32_t* max_deg, uint32_t* max_w,
+                   uint32_t* min_w, uint32_t* highd0);
+
+/* Copy the CSR to host arrays: row_ptr[n+1] (uint64), nbr[2m], w[2m]; and
+ * RtoW[EIC_RATIO_NUM] when rtow is non-NULL. Any array may be NULL. */
+int eic_graph_export(const eic_graph* g, uint64_t* row_ptr, uint32_t* nbr, uint32_t* w, uint32_t* rtow);
+
+/* Device bytes held by the graph and by its query workspace. */
+int eic_graph_memory(const eic_graph* g, uint64_t* graph_bytes, uint64_t* workspace_bytes);
+
+/* Free the graph and its workspace. NULL is accepted. Must not race a query
+ * on the same graph. */
+int eic_graph_destroy(eic_graph* g);
+
+/*
+ * One single-source query by Algorithm 1 (dynamic stepping, Eq. 1-3;
+ * traversal optimisation, Function 1/2), exact distances.
+ *   source   0 <= source < n.
+ *   dist     device array of n uint32, caller-owned; receives lsp(source, v)
+ *            or EIC_INF.
+ *   parent   device array of n uint32 or NULL; receives the smallest-id u
+ *            with dist[u] + w(u, v) == dist[v] (parent[source] = source,
+ *            EIC_INF where unreachable).
+ *   params   NULL for eic_params_default().
+ *   stats    NULL, or a host struct that receives the counters (and the
+ *            trace rows when stats->trace is set).
+ *   stream   the work is enqueued on it; the call synchronises the stream
+ *            before returning the status.
+ * The graph's workspace is allocated on first use (device memory about 30
+ * bytes per vertex plus the heavy-window and step tables); concurrent calls
+ * on one graph are serialised.
+ * Errors: EIC_EINVAL, EIC_ENOMEM, EIC_ECUDA, EIC_EOVERFLOW (dist is then
+ * unspecified), EIC_ETIMEOUT.
+ */
+int eic_sssp(const eic_graph* g, uint32_t source, uint32_t* dist, uint32_t* parent, const eic_params* params,
+             eic_stats* stats, void* stream);
+
+/*
+ * num_queries queries (graphs[i], sources[i]) -> dists[i], with the same
+ * semantics as eic_sssp. graphs and sources are host arrays; dists is a host
+ * array of device pointers, one n_i-element uint32 buffer per query.
+ * statuses (host array of num_queries ints, or NULL) receives each query's
+ * status; the return value is the first non-OK status, or EIC_OK.
+ * The queries are enqueued back to back on stream without host round trips;
+ * the call synchronises once at the end.
+ */
+int eic_sssp_batch(const eic_graph* const* graphs, const uint32_t* sources, uint32_t num_queries,
+                   uint32_t* const* dists, const eic_params* params, int* statuses, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* EIC_H */

@@ -1,0 +1,234 @@
+"""Thin ctypes binding over libeic (include/eic.h). Argument marshalling only.
+
+Every step of a query runs in libeic's CUDA kernels; this module passes
+pointers and sizes. PyTorch supplies device memory and streams. There is no
+CPU fallback: loading fails loudly when the library or a CUDA device is
+missing.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libeic.so")
+
+EIC_INF = 0xFFFFFFFF
+RATIO_NUM = 4096
+OK, EINVAL, ENOMEM, ECUDA, EOVERFLOW, ETIMEOUT, EBUSY = range(7)
+FLAG_NO_PULL = 1
+
+# Every name declared in include/eic.h.
+EXPORTS = ("eic_params_default", "eic_strerror", "eic_version", "eic_graph_create", "eic_graph_info",
+           "eic_graph_export", "eic_graph_memory", "eic_graph_destroy", "eic_sssp", "eic_sssp_batch")
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("alpha", ctypes.c_uint32), ("beta", ctypes.c_double), ("st_num", ctypes.c_uint32),
+                ("gap_shift", ctypes.c_uint32), ("block_threads", ctypes.c_uint32), ("heavy_min", ctypes.c_uint32),
+                ("max_spin_log2", ctypes.c_uint32), ("flags", ctypes.c_uint32), ("reserved", ctypes.c_uint32 * 8)]
+
+
+class Step(ctypes.Structure):
+    _fields_ = [("lb", ctypes.c_int64), ("ub", ctypes.c_int64), ("st", ctypes.c_int64), ("gap_lb", ctypes.c_int64),
+                ("sumd_lb", ctypes.c_uint64), ("highd_lb", ctypes.c_uint64), ("rounds", ctypes.c_uint64),
+                ("settled", ctypes.c_uint64)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("steps", ctypes.c_uint64), ("rounds", ctypes.c_uint64), ("frontier", ctypes.c_uint64),
+                ("traversed", ctypes.c_uint64), ("pulls", ctypes.c_uint64), ("improved", ctypes.c_uint64),
+                ("heavy", ctypes.c_uint64), ("trace", ctypes.POINTER(Step)), ("trace_cap", ctypes.c_uint64),
+                ("trace_len", ctypes.c_uint64)]
+
+
+class EicError(RuntimeError):
+    def __init__(self, status: int, what: str = ""):
+        self.status = status
+        super().__init__(f"{what}: {strerror(status)} ({status})" if what else f"{strerror(status)} ({status})")
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def load_library(path: str | None = None):
+    """Load libeic.so (raises if it is absent: no fallback path exists)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        p = path or LIB_PATH
+        if not os.path.exists(p):
+            raise RuntimeError(f"libeic.so not found at {p}: build it first (paper_2506_19349_gb300.build)")
+        L = ctypes.CDLL(p)
+        vp, u32, u64, c_int = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int
+        L.eic_params_default.argtypes = [ctypes.POINTER(Params)]
+        L.eic_params_default.restype = c_int
+        L.eic_strerror.argtypes = [c_int]
+        L.eic_strerror.restype = ctypes.c_char_p
+        L.eic_version.argtypes = []
+        L.eic_version.restype = c_int
+        L.eic_graph_create.argtypes = [vp, vp, vp, u64, u32, c_int, vp, ctypes.POINTER(vp)]
+        L.eic_graph_create.restype = c_int
+        L.eic_graph_info.argtypes = [vp] + [ctypes.POINTER(u32), ctypes.POINTER(u64)] + [ctypes.POINTER(u32)] * 4
+        L.eic_graph_info.restype = c_int
+        L.eic_graph_export.argtypes = [vp, vp, vp, vp, vp]
+        L.eic_graph_export.restype = c_int
+        L.eic_graph_memory.argtypes = [vp, ctypes.POINTER(u64), ctypes.POINTER(u64)]
+        L.eic_graph_memory.restype = c_int
+        L.eic_graph_destroy.argtypes = [vp]
+        L.eic_graph_destroy.restype = c_int
+        L.eic_sssp.argtypes = [vp, u32, vp, vp, ctypes.POINTER(Params), ctypes.POINTER(Stats), vp]
+        L.eic_sssp.restype = c_int
+        L.eic_sssp_batch.argtypes = [ctypes.POINTER(vp), vp, u32, ctypes.POINTER(vp), ctypes.POINTER(Params), vp, vp]
+        L.eic_sssp_batch.restype = c_int
+        _lib = L
+        return L
+
+
+def strerror(status: int) -> str:
+    try:
+        return load_library().eic_strerror(status).decode()
+    except Exception:  # pragma: no cover - only when the library cannot load
+        return f"status {status}"
+
+
+def default_params(**overrides) -> Params:
+    p = Params()
+    load_library().eic_params_default(ctypes.byref(p))
+    for k, v in overrides.items():
+        setattr(p, k, v)
+    return p
+
+
+def _torch():
+    import torch
+
+    if not torch.cuda.is_available():
+        raise RuntimeError("libeic needs a CUDA device")
+    return torch
+
+
+def _stream_ptr(stream) -> int:
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return int(s.cuda_stream)
+
+
+def _check(status: int, what: str):
+    if status != OK:
+        raise EicError(status, what)
+
+
+class Graph:
+    """Device-resident graph (eic_graph_create / eic_graph_destroy)."""
+
+    def __init__(self, n: int, src, dst, w, stream=None):
+        torch = _torch()
+        L = load_library()
+        self._h = ctypes.c_void_p()
+        keep = []
+        if isinstance(src, torch.Tensor) and src.is_cuda:
+            t = [x.contiguous() for x in (src, dst, w)]
+            assert all(x.dtype in (torch.int32, torch.uint32) for x in t)
+            keep = t
+            ptrs = [x.data_ptr() for x in t]
+            num, on_dev = t[0].numel(), 1
+        else:
+            a = [np.ascontiguousarray(x, dtype=np.uint32) for x in (src, dst, w)]
+            keep = a
+            ptrs = [x.ctypes.data for x in a]
+            num, on_dev = a[0].size, 0
+        st = _stream_ptr(stream)
+        rc = L.eic_graph_create(ptrs[0], ptrs[1], ptrs[2], num, n, on_dev, st, ctypes.byref(self._h))
+        del keep
+        _check(rc, "eic_graph_create")
+        nn, m, md, mw, mi, h0 = (ctypes.c_uint32(), ctypes.c_uint64(), ctypes.c_uint32(), ctypes.c_uint32(),
+                                 ctypes.c_uint32(), ctypes.c_uint32())
+        _check(L.eic_graph_info(self._h, ctypes.byref(nn), ctypes.byref(m), ctypes.byref(md), ctypes.byref(mw),
+                                ctypes.byref(mi), ctypes.byref(h0)), "eic_graph_info")
+        self.n, self.m, self.max_deg, self.max_w, self.min_w, self.highd0 = (nn.value, m.value, md.value, mw.value,
+                                                                            mi.value, h0.value)
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value and _lib is not None:
+            _lib.eic_graph_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def export(self):
+        """(row_ptr uint64[n+1], nbr uint32[2m], w uint32[2m], rtow uint32[4096]) on the host."""
+        row = np.empty(self.n + 1, dtype=np.uint64)
+        nbr = np.empty(2 * self.m, dtype=np.uint32)
+        w = np.empty(2 * self.m, dtype=np.uint32)
+        rt = np.empty(RATIO_NUM, dtype=np.uint32)
+        _check(load_library().eic_graph_export(self._h, row.ctypes.data, nbr.ctypes.data, w.ctypes.data,
+                                               rt.ctypes.data), "eic_graph_export")
+        return row, nbr, w, rt
+
+    def memory(self):
+        gb, wb = ctypes.c_uint64(), ctypes.c_uint64()
+        _check(load_library().eic_graph_memory(self._h, ctypes.byref(gb), ctypes.byref(wb)), "eic_graph_memory")
+        return gb.value, wb.value
+
+
+def new_dist(n: int, device=None):
+    torch = _torch()
+    return torch.empty(n, dtype=torch.int32, device=device or "cuda")
+
+
+def sssp(graph: Graph, source: int, dist=None, parent=None, params: Params | None = None, stats: bool = False,
+         trace_cap: int = 0, stream=None, raise_on_error: bool = True):
+    """One query. Returns (dist, status, stats_dict or None); dist is an int32
+    CUDA tensor holding uint32 distances (0xFFFFFFFF = unreachable)."""
+    L = load_library()
+    if dist is None:
+        dist = new_dist(graph.n)
+    st = Stats()
+    rows = None
+    if trace_cap:
+        rows = (Step * trace_cap)()
+        st.trace = ctypes.cast(rows, ctypes.POINTER(Step))
+        st.trace_cap = trace_cap
+    rc = L.eic_sssp(graph.handle, int(source), dist.data_ptr(), parent.data_ptr() if parent is not None else None,
+                    ctypes.byref(params) if params is not None else None, ctypes.byref(st) if (stats or trace_cap)
+                    else None, _stream_ptr(stream))
+    if raise_on_error:
+        _check(rc, "eic_sssp")
+    info = None
+    if stats or trace_cap:
+        info = {f: getattr(st, f) for f, _ in Stats._fields_ if f not in ("trace", "trace_cap")}
+        if rows is not None:
+            info["trace"] = [{f: getattr(rows[i], f) for f, _ in Step._fields_}
+                             for i in range(min(st.trace_len, trace_cap))]
+    return dist, rc, info
+
+
+def sssp_batch(graphs, sources, dists, params: Params | None = None, stream=None):
+    """Queries (graphs[i], sources[i]) -> dists[i] (CUDA tensors); returns the statuses."""
+    L = load_library()
+    q = len(sources)
+    harr = (ctypes.c_void_p * q)(*[g.handle.value for g in graphs])
+    srcs = np.ascontiguousarray(sources, dtype=np.uint32)
+    darr = (ctypes.c_void_p * q)(*[d.data_ptr() for d in dists])
+    statuses = np.zeros(q, dtype=np.int32)
+    L.eic_sssp_batch(harr, srcs.ctypes.data, q, darr, ctypes.byref(params) if params is not None else None,
+                     statuses.ctypes.data, _stream_ptr(stream))
+    return statuses
+
+
+def to_host_u32(t) -> np.ndarray:
+    return t.detach().cpu().numpy().view(np.uint32)

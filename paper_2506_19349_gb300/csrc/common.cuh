@@ -1,0 +1,118 @@
+// Shared definitions of libeic's CUDA sources (sm_103a).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/eic.h"
+
+#define EIC_INF_T (((int64_t)1) << 62)
+#define EIC_FULL_MASK 0xFFFFFFFFu
+
+#define EIC_CUDA_TRY(expr)                     \
+  do {                                         \
+    cudaError_t e_ = (expr);                   \
+    if (e_ != cudaSuccess) {                   \
+      (void)cudaGetLastError();                \
+      return e_ == cudaErrorMemoryAllocation   \
+                 ? EIC_ENOMEM                  \
+                 : EIC_ECUDA;                  \
+    }                                          \
+  } while (0)
+
+// Read-only view of a device-resident graph (preprocessing of Section 4.1).
+struct DevGraph {
+  uint32_t n;
+  uint64_t two_m;         // directed entries, sum of degrees
+  uint64_t m;             // undirected edges
+  const uint64_t* row;    // [n + 1]
+  const uint2* adj;       // [two_m] {neighbour, weight}, rows sorted by (weight, neighbour)
+  const uint32_t* drank;  // [max_deg + 1] degree -> rank among distinct degrees (present ones)
+  const uint32_t* dvals;  // [D] distinct degrees >= 1, ascending
+  const uint32_t* dcnt0;  // [D] number of vertices with degree dvals[r]
+  uint32_t D;
+  const uint32_t* rtow;   // [EIC_RATIO_NUM] maxW(G, i / (RATIO_NUM - 1))
+  const uint32_t* nz;     // [nz_count] vertices with degree >= 1, ascending
+  uint32_t nz_count;
+  uint32_t maxw, minw, max_deg, highd0;
+};
+
+// ------------------------------------------------------------ warp helpers
+
+__device__ __forceinline__ uint32_t lane_id() { return threadIdx.x & 31u; }
+
+__device__ __forceinline__ uint32_t warp_incl_scan(uint32_t x) {
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    uint32_t y = __shfl_up_sync(EIC_FULL_MASK, x, o);
+    if ((int)lane_id() >= o) x += y;
+  }
+  return x;
+}
+
+__device__ __forceinline__ uint64_t warp_sum_u64(uint64_t x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(EIC_FULL_MASK, x, o);
+  return x;
+}
+
+// Warp-aggregated append of `item` for each lane with want != 0 to
+// list[*counter ...]; returns the slot or UINT32_MAX. All lanes must call.
+__device__ __forceinline__ uint32_t warp_append(bool want, uint32_t* counter) {
+  uint32_t mask = __ballot_sync(EIC_FULL_MASK, want);
+  if (mask == 0) return UINT32_MAX;
+  uint32_t leader = __ffs(mask) - 1;
+  uint32_t base = 0;
+  if (lane_id() == leader) base = atomicAdd(counter, (uint32_t)__popc(mask));
+  base = __shfl_sync(EIC_FULL_MASK, base, leader);
+  return want ? base + __popc(mask & ((1u << lane_id()) - 1u)) : UINT32_MAX;
+}
+
+__device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t* p) {
+  uint32_t v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ int ld_volatile_int(const int* p) { return *(const volatile int*)p; }
+
+// ---------------------------------------------------- bounded grid barrier
+
+struct GridBarrier {
+  uint32_t count;
+  uint32_t gen;
+};
+
+// Software grid barrier for a co-resident (cooperatively launched) grid.
+// Every wait is bounded: after max_spin polls the block records
+// EIC_ETIMEOUT in *status and all blocks leave at their next barrier. Returns
+// false when the kernel must stop (any block reported an error).
+__device__ __forceinline__ bool grid_barrier(GridBarrier* bar, uint32_t* gen_local, uint64_t max_spin, int* status) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t g = *gen_local;
+    __threadfence();
+    uint32_t arrived = atomicAdd(&bar->count, 1u);
+    if (arrived == gridDim.x - 1) {
+      bar->count = 0;
+      __threadfence();
+      atomicExch(&bar->gen, g + 1);
+    } else {
+      uint64_t spins = 0;
+      while (ld_acquire_u32(&bar->gen) == g) {
+        if (ld_volatile_int(status) != 0) break;
+        if (++spins > max_spin) {
+          atomicCAS(status, 0, EIC_ETIMEOUT);
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    *gen_local = g + 1;
+    __threadfence();
+    s_ok = ld_volatile_int(status) == 0;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}

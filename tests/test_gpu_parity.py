@@ -1,0 +1,209 @@
+"""GPU parity: libeic against the CPU oracle, element by element.
+
+Distances are uint32 and must match Dijkstra bit for bit. The device CSR must
+equal the oracle's CSR byte for byte; RtoW and highD(0) must match exactly;
+the per-step trace <lb, ub, st> with its statistics must equal the oracle's
+sequential Algorithm 1 (every quantity is a function of the exact distances).
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2506_19349_gb300 import graphgen as G
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import paper_2506_19349_gb300 as eic  # noqa: E402
+from paper_2506_19349_gb300 import binding  # noqa: E402
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2506_19349_gb300 import build
+
+    build.build()
+
+
+def _pair(wl):
+    return eic.Graph(wl.n, wl.src, wl.dst, wl.w), O.Graph(wl.n, wl.src, wl.dst, wl.w)
+
+
+def _cases():
+    yield "urand14", G.urand(14, 17, seed=1, nsources=4)
+    yield "urand12_sparse", G.urand(12, 12, seed=8, nsources=4)
+    yield "kron10", G.kron(10, seed=20, nsources=4)
+    yield "kron14", G.kron(14, seed=21, nsources=4)
+    yield "kron16", G.kron(16, seed=2, nsources=3)
+    yield "kron13_lognormal", G.kron(13, seed=22, weights="lognormal", nsources=3)
+    yield "grid64", G.road(64, seed=23, wmax=4095, nsources=3)
+    yield "grid128_w255", G.road(128, seed=24, wmax=255, nsources=2)
+    w = G.kron(12, seed=25, nsources=3)
+    w.w = np.ones_like(w.w)
+    yield "kron12_unit", w
+    w = G.kron(12, seed=26, nsources=3)
+    w.w = (w.w % 3 + 1).astype(np.uint32)
+    yield "kron12_w123", w
+
+
+CASES = list(_cases())
+
+
+@pytest.mark.parametrize("name,wl", CASES, ids=[c[0] for c in CASES])
+def test_csr_equals_oracle(name, wl):
+    g, og = _pair(wl)
+    row, nbr, w, rt = g.export()
+    orow, onbr, ow = og.csr()
+    assert np.array_equal(row, orow)
+    assert np.array_equal(nbr, onbr)
+    assert np.array_equal(w, ow)
+    assert np.array_equal(rt, og.rtow())
+    assert g.highd0 == O.highd(og.degrees())
+    assert (g.m, g.max_w, g.max_deg) == (og.m, og.maxw, og.maxdeg)
+
+
+@pytest.mark.parametrize("name,wl", CASES, ids=[c[0] for c in CASES])
+def test_distances_bit_exact_and_trace(name, wl):
+    g, og = _pair(wl)
+    for s in wl.sources:
+        s = int(s)
+        dist, rc, info = eic.sssp(g, s, trace_cap=4096)
+        got = eic.to_host_u32(dist)
+        want, orc = og.dijkstra(s)
+        assert rc == 0 and orc == 0
+        mism = np.flatnonzero(got != want)
+        assert mism.size == 0, f"{name} s={s}: {mism.size} mismatches, first {mism[:5]} got {got[mism[:5]]} " \
+                               f"want {want[mism[:5]]}"
+        assert og.check(s, got) == (0, 0)
+        _, _, otrace, otot = og.eic(s)
+        keys = ("lb", "ub", "st", "gap_lb", "sumd_lb", "highd_lb", "settled")
+        gt = [{k: r[k] for k in keys} for r in info["trace"]]
+        ot = [{k: r[k] for k in keys} for r in otrace]
+        assert gt == ot, f"{name} s={s}: trace differs at step {next(i for i, (a, b) in enumerate(zip(gt, ot)) if a != b) if len(gt) == len(ot) else 'len'}"
+        assert info["steps"] == otot["steps"]
+
+
+def test_parent_output():
+    wl = G.kron(12, seed=30, nsources=2)
+    g, og = _pair(wl)
+    for s in wl.sources:
+        par = torch.empty(wl.n, dtype=torch.int32, device="cuda")
+        dist, rc, _ = eic.sssp(g, int(s), parent=par)
+        d = eic.to_host_u32(dist)
+        assert np.array_equal(eic.to_host_u32(par), og.parent(int(s), d))
+
+
+def test_no_pull_and_step_scaling_stay_exact():
+    wl = G.kron(14, seed=31, nsources=2)
+    g, og = _pair(wl)
+    for s in wl.sources:
+        want, _ = og.dijkstra(int(s))
+        for p in (eic.default_params(flags=eic.FLAG_NO_PULL), eic.default_params(gap_shift=2),
+                  eic.default_params(heavy_min=256), eic.default_params(block_threads=256),
+                  eic.default_params(st_num=7)):
+            dist, rc, _ = eic.sssp(g, int(s), params=p)
+            assert np.array_equal(eic.to_host_u32(dist), want)
+
+
+def test_edge_cases():
+    # single vertex, no edges
+    g = eic.Graph(1, np.zeros(0, np.uint32), np.zeros(0, np.uint32), np.zeros(0, np.uint32))
+    d, rc, _ = eic.sssp(g, 0)
+    assert eic.to_host_u32(d).tolist() == [0]
+    # self-loops and duplicates only around an isolated source
+    src = np.array([0, 1, 1, 2, 2], np.uint32)
+    dst = np.array([0, 2, 2, 1, 3], np.uint32)
+    w = np.array([5, 9, 4, 7, 1], np.uint32)
+    g = eic.Graph(5, src, dst, w)
+    d, _, _ = eic.sssp(g, 0)
+    assert eic.to_host_u32(d).tolist() == [0, eic.EIC_INF, eic.EIC_INF, eic.EIC_INF, eic.EIC_INF]
+    d, _, _ = eic.sssp(g, 1)
+    assert eic.to_host_u32(d).tolist() == [eic.EIC_INF, 0, 4, 5, eic.EIC_INF]
+    # long path: many rounds in one step
+    n = 3000
+    src = np.arange(n - 1, dtype=np.uint32)
+    g = eic.Graph(n, src, src + 1, (src % 7 + 1).astype(np.uint32))
+    d, _, _ = eic.sssp(g, 0)
+    assert np.array_equal(eic.to_host_u32(d), np.concatenate([[0], np.cumsum(src % 7 + 1)]).astype(np.uint32))
+    # star: hub source (the first step's ub becomes 0) and leaf source
+    n = 5000
+    leaves = np.arange(1, n, dtype=np.uint32)
+    ww = (leaves % 250 + 1).astype(np.uint32)
+    g = eic.Graph(n, np.zeros(n - 1, np.uint32), leaves, ww)
+    og = O.Graph(n, np.zeros(n - 1, np.uint32), leaves, ww)
+    for s in (0, 17, n - 1):
+        d, _, _ = eic.sssp(g, s)
+        assert np.array_equal(eic.to_host_u32(d), og.dijkstra(s)[0])
+
+
+def test_hub_sources_kron():
+    wl = G.kron(15, seed=32, nsources=1)
+    g, og = _pair(wl)
+    deg = og.degrees()
+    for s in np.argsort(deg)[-3:]:  # highest-degree vertices: deg(s) >= highD(0)
+        d, _, info = eic.sssp(g, int(s), trace_cap=256)
+        assert np.array_equal(eic.to_host_u32(d), og.dijkstra(int(s))[0])
+        assert info["trace"][0]["ub"] == 0
+
+
+def test_errors():
+    wl = G.urand(10, 12, seed=3)
+    g = eic.Graph(wl.n, wl.src, wl.dst, wl.w)
+    _, rc, _ = eic.sssp(g, wl.n, raise_on_error=False)
+    assert rc == binding.EINVAL
+    with pytest.raises(eic.EicError) as e:
+        eic.Graph(4, np.array([0, 1], np.uint32), np.array([1, 2], np.uint32), np.array([3, 0], np.uint32))
+    assert e.value.status == binding.EINVAL
+    with pytest.raises(eic.EicError):
+        eic.Graph(4, np.array([0, 1], np.uint32), np.array([1, 4], np.uint32), np.array([3, 1], np.uint32))
+    # overflow: the largest distance plus the largest weight reaches 2^32-1
+    w = np.array([2_000_000_000, 2_000_000_000, 200_000_000], np.uint32)
+    g = eic.Graph(4, np.arange(3, dtype=np.uint32), np.arange(1, 4, dtype=np.uint32), w)
+    _, rc, _ = eic.sssp(g, 0, raise_on_error=False)
+    assert rc == binding.EOVERFLOW
+    w2 = np.array([1_000_000_000, 1_000_000_000, 100], np.uint32)
+    g = eic.Graph(4, np.arange(3, dtype=np.uint32), np.arange(1, 4, dtype=np.uint32), w2)
+    d, rc, _ = eic.sssp(g, 0)
+    assert eic.to_host_u32(d).tolist() == [0, 1_000_000_000, 2_000_000_000, 2_000_000_100]
+
+
+def test_barrier_timeout_is_reported_and_context_survives():
+    wl = G.kron(12, seed=33, nsources=1)
+    g, og = _pair(wl)
+    p = eic.default_params(max_spin_log2=1)  # two polls: waiting blocks give up at once
+    _, rc, _ = eic.sssp(g, int(wl.sources[0]), params=p, raise_on_error=False)
+    assert rc in (binding.ETIMEOUT, binding.OK)
+    d, rc, _ = eic.sssp(g, int(wl.sources[0]))
+    assert rc == 0 and np.array_equal(eic.to_host_u32(d), og.dijkstra(int(wl.sources[0]))[0])
+
+
+def test_batch_equals_single_queries():
+    wls = [G.kron(11, seed=40, nsources=3), G.road(48, seed=41, wmax=255, nsources=3), G.urand(11, 14, seed=42,
+                                                                                                 nsources=3)]
+    graphs, srcs, dists, want = [], [], [], []
+    for wl in wls:
+        g, og = _pair(wl)
+        for s in wl.sources:
+            graphs.append(g)
+            srcs.append(int(s))
+            dists.append(eic.new_dist(wl.n))
+            want.append(og.dijkstra(int(s))[0])
+    st = eic.sssp_batch(graphs, srcs, dists)
+    assert (st == 0).all()
+    for d, w in zip(dists, want):
+        assert np.array_equal(eic.to_host_u32(d), w)
+
+
+def test_counters_in_paper_bands():
+    wl = G.kron(16, seed=2, nsources=2)
+    g, og = _pair(wl)
+    for s in wl.sources:
+        d, _, info = eic.sssp(g, int(s), stats=True)
+        reach = int((eic.to_host_u32(d) != eic.EIC_INF).sum())
+        assert info["frontier"] / reach <= 1.2
+        assert 2.0 <= info["traversed"] / reach <= 7.0
