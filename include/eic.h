@@ -46,9 +46,10 @@ typedef struct eic_graph eic_graph;
  *   gap_shift     step-width multiplier 2^gap_shift applied to Eq. 3's gap
  *                 (0 = the paper; any value keeps distances exact).
  *   block_threads threads per block of the relaxation kernel (0 = library
- *                 choice; else a multiple of 32 in [128, 1024]).
- *   heavy_min     window length above which a vertex's edges are spread over
- *                 the whole grid instead of one warp (0 = library choice).
+ *                 choice; else a multiple of 32 in [128, 512]).
+ *   heavy_min     window length above which a vertex's edges are cut into
+ *                 64-entry tasks spread over the whole grid instead of being
+ *                 relaxed by one warp (0 = library choice, 32; else 16..4096).
  *   max_spin_log2 bound on each grid-barrier wait, 2^max_spin_log2 polls of
  *                 about 100 ns (0 = library choice, about 2 s); exceeding it
  *                 returns EIC_ETIMEOUT.
@@ -89,10 +90,18 @@ typedef struct {
   uint64_t traversed;  /* nTrav: window entries relaxed plus pull requests */
   uint64_t pulls;      /* pull requests (entries examined by Function 1's pull) */
   uint64_t improved;   /* successful relaxations */
-  uint64_t heavy;      /* vertex windows spread over the grid */
+  uint64_t heavy;      /* 64-entry tasks spread over the grid */
   eic_step* trace;
   uint64_t trace_cap;
   uint64_t trace_len;
+  /* Diagnostic timeline: when timeline is a host array of 2 * timeline_cap
+   * uint64, it receives (device globaltimer ns, tag) pairs: one per grid
+   * barrier and around each step-boundary evaluation. tag = kind << 32 |
+   * round id, kind 0 kernel start, 1 round, 2 heavy phase, 3 step, 4/5
+   * step-boundary begin/end. */
+  uint64_t* timeline;
+  uint64_t timeline_cap;
+  uint64_t timeline_len;
 } eic_stats;
 
 /* Fill *p with the paper's defaults (Section 4.1). Returns EIC_EINVAL if p is NULL. */

@@ -42,7 +42,8 @@ class Stats(ctypes.Structure):
     _fields_ = [("steps", ctypes.c_uint64), ("rounds", ctypes.c_uint64), ("frontier", ctypes.c_uint64),
                 ("traversed", ctypes.c_uint64), ("pulls", ctypes.c_uint64), ("improved", ctypes.c_uint64),
                 ("heavy", ctypes.c_uint64), ("trace", ctypes.POINTER(Step)), ("trace_cap", ctypes.c_uint64),
-                ("trace_len", ctypes.c_uint64)]
+                ("trace_len", ctypes.c_uint64), ("timeline", ctypes.POINTER(ctypes.c_uint64)),
+                ("timeline_cap", ctypes.c_uint64), ("timeline_len", ctypes.c_uint64)]
 
 
 class EicError(RuntimeError):
@@ -191,7 +192,7 @@ def new_dist(n: int, device=None):
 
 
 def sssp(graph: Graph, source: int, dist=None, parent=None, params: Params | None = None, stats: bool = False,
-         trace_cap: int = 0, stream=None, raise_on_error: bool = True):
+         trace_cap: int = 0, stream=None, raise_on_error: bool = True, timeline_cap: int = 0):
     """One query. Returns (dist, status, stats_dict or None); dist is an int32
     CUDA tensor holding uint32 distances (0xFFFFFFFF = unreachable)."""
     L = load_library()
@@ -203,14 +204,24 @@ def sssp(graph: Graph, source: int, dist=None, parent=None, params: Params | Non
         rows = (Step * trace_cap)()
         st.trace = ctypes.cast(rows, ctypes.POINTER(Step))
         st.trace_cap = trace_cap
+    tl = None
+    if timeline_cap:
+        tl = np.zeros(2 * timeline_cap, dtype=np.uint64)
+        st.timeline = tl.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64))
+        st.timeline_cap = timeline_cap
+    want = stats or trace_cap or timeline_cap
     rc = L.eic_sssp(graph.handle, int(source), dist.data_ptr(), parent.data_ptr() if parent is not None else None,
-                    ctypes.byref(params) if params is not None else None, ctypes.byref(st) if (stats or trace_cap)
-                    else None, _stream_ptr(stream))
+                    ctypes.byref(params) if params is not None else None, ctypes.byref(st) if want else None,
+                    _stream_ptr(stream))
     if raise_on_error:
         _check(rc, "eic_sssp")
     info = None
-    if stats or trace_cap:
-        info = {f: getattr(st, f) for f, _ in Stats._fields_ if f not in ("trace", "trace_cap")}
+    if want:
+        info = {f: getattr(st, f) for f, _ in Stats._fields_ if f not in ("trace", "trace_cap", "timeline",
+                                                                           "timeline_cap")}
+        if tl is not None:
+            k = min(st.timeline_len, timeline_cap)
+            info["timeline"] = tl[:2 * k].reshape(k, 2)
         if rows is not None:
             info["trace"] = [{f: getattr(rows[i], f) for f, _ in Step._fields_}
                              for i in range(min(st.trace_len, trace_cap))]

@@ -25,15 +25,17 @@ struct DevGraph {
   uint32_t n;
   uint64_t two_m;         // directed entries, sum of degrees
   uint64_t m;             // undirected edges
-  const uint64_t* row;    // [n + 1]
+  const uint32_t* row;    // [n + 1] row offsets (2m < 2^32)
   const uint2* adj;       // [two_m] {neighbour, weight}, rows sorted by (weight, neighbour)
   const uint32_t* drank;  // [max_deg + 1] degree -> rank among distinct degrees (present ones)
   const uint32_t* dvals;  // [D] distinct degrees >= 1, ascending
   const uint32_t* dcnt0;  // [D] number of vertices with degree dvals[r]
   uint32_t D;
   const uint32_t* rtow;   // [EIC_RATIO_NUM] maxW(G, i / (RATIO_NUM - 1))
-  const uint32_t* nz;     // [nz_count] vertices with degree >= 1, ascending
+  const uint2* nz;        // [nz_count] {vertex, smallest row weight} for degree >= 1, by (weight, vertex)
   uint32_t nz_count;
+  const uint32_t* nz_lt;  // [nz_lt_len] nz_lt[t] = number of nz entries with smallest weight < t
+  uint32_t nz_lt_len;
   uint32_t maxw, minw, max_deg, highd0;
 };
 

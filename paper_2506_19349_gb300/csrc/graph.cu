@@ -190,15 +190,41 @@ __global__ void k_highd0(const uint32_t* dcnt0, const uint32_t* dvals, uint32_t 
   if (threadIdx.x == 0) *out = h;
 }
 
+__global__ void k_narrow(const uint64_t* __restrict__ in, uint64_t n, uint32_t* out) {
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x)
+    out[i] = (uint32_t)in[i];
+}
+
+__global__ void k_nz_keys(const uint2* __restrict__ nz, uint32_t cnt, int vbits, uint64_t* keys) {
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += gridDim.x * blockDim.x)
+    keys[i] = ((uint64_t)nz[i].y << vbits) | nz[i].x;
+}
+
+__global__ void k_nz_from_keys(const uint64_t* __restrict__ keys, uint32_t cnt, int vbits, uint2* nz) {
+  const uint64_t vmask = (1ull << vbits) - 1;
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += gridDim.x * blockDim.x)
+    nz[i] = make_uint2((uint32_t)(keys[i] & vmask), (uint32_t)(keys[i] >> vbits));
+}
+
+// lt[t] = number of entries of the weight-sorted nz with smallest weight < t, t < len
+__global__ void k_nz_lt(const uint2* __restrict__ nz, uint32_t cnt, uint32_t len, uint32_t* lt) {
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i <= cnt; i += gridDim.x * blockDim.x) {
+    const uint32_t lo = i == 0 ? 0 : nz[i - 1].y + 1;           // first t with entry i-1 counted
+    const uint32_t hi = i == cnt ? len - 1 : nz[i].y;           // last t before entry i counts
+    for (uint32_t t = lo; t <= hi && t < len; ++t) lt[t] = i;
+  }
+}
+
 __global__ void k_flag_nonzero(const uint32_t* __restrict__ deg, uint32_t n, uint32_t* flags) {
   for (uint64_t v = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; v < n; v += (uint64_t)gridDim.x * blockDim.x)
     flags[v] = deg[v] ? 1u : 0u;
 }
 
-__global__ void k_scatter_nz(const uint32_t* __restrict__ flags, const uint64_t* __restrict__ pos, uint32_t n,
-                             uint32_t* nz) {
+// nz[k] = {v, smallest weight of v's row} for the k-th vertex with degree >= 1
+__global__ void k_scatter_nz(const uint32_t* __restrict__ flags, const uint64_t* __restrict__ pos,
+                             const uint32_t* __restrict__ row, const uint2* __restrict__ adj, uint32_t n, uint2* nz) {
   for (uint64_t v = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; v < n; v += (uint64_t)gridDim.x * blockDim.x)
-    if (flags[v]) nz[pos[v]] = (uint32_t)v;
+    if (flags[v]) nz[pos[v]] = make_uint2((uint32_t)v, adj[row[v]].y);
 }
 
 // Temporary device allocations released on every exit path.
@@ -255,6 +281,7 @@ void graph_free_arrays(eic_graph* g) {
   cudaFree(g->dcnt0);
   cudaFree(g->rtow);
   cudaFree(g->nz);
+  cudaFree(g->nz_lt);
 }
 
 int build(eic_graph* g, const uint32_t* src, const uint32_t* dst, const uint32_t* w, uint64_t T, uint32_t n,
@@ -347,7 +374,15 @@ int build(eic_graph* g, const uint32_t* src, const uint32_t* dst, const uint32_t
   EIC_CUDA_TRY(cudaMemsetAsync(deg, 0, ((uint64_t)n + 1) * 4, st));
   if (m > 0) k_degrees<<<grid_for(m), kThreads, 0, st>>>(ukeys, uw, m, vbits, deg, small + 1, small + 2);
   TRY(galloc(g, &g->row, (uint64_t)n + 1));
-  TRY(exclusive_scan<uint32_t>(deg, n, g->row, scan_scratch, st));
+  {
+    uint64_t* row64;
+    TRY(tmp.alloc(&row64, (uint64_t)n + 1));
+    TRY(exclusive_scan<uint32_t>(deg, n, row64, scan_scratch, st));
+    k_narrow<<<grid_for((uint64_t)n + 1), kThreads, 0, st>>>(row64, (uint64_t)n + 1, g->row);
+    EIC_CUDA_TRY(cudaGetLastError());
+    EIC_CUDA_TRY(cudaStreamSynchronize(st));
+    tmp.release(row64);
+  }
   EIC_CUDA_TRY(cudaMemcpyAsync(hs, small, sizeof(hs), cudaMemcpyDeviceToHost, st));
   EIC_CUDA_TRY(cudaStreamSynchronize(st));
   const uint32_t maxw = m ? hs[1] : 0, minw = m ? hs[2] : 0;
@@ -423,8 +458,8 @@ int build(eic_graph* g, const uint32_t* src, const uint32_t* dst, const uint32_t
     EIC_CUDA_TRY(cudaGetLastError());
   }
 
-  // 5c. non-isolated vertices, ascending
-  uint32_t nzc = 0;
+  // 5c. non-isolated vertices with their smallest weight
+  uint32_t nzc = 0, nz_lt_len = 0;
   {
     uint32_t* flags;
     uint64_t* pos;
@@ -437,7 +472,26 @@ int build(eic_graph* g, const uint32_t* src, const uint32_t* dst, const uint32_t
     EIC_CUDA_TRY(cudaStreamSynchronize(st));
     nzc = (uint32_t)c;
     TRY(galloc(g, &g->nz, nzc));
-    k_scatter_nz<<<grid_for(n), kThreads, 0, st>>>(flags, pos, n, g->nz);
+    k_scatter_nz<<<grid_for(n), kThreads, 0, st>>>(flags, pos, g->row, g->adj, n, g->nz);
+    EIC_CUDA_TRY(cudaGetLastError());
+    // order by (smallest weight, vertex): the vertices a pull can touch (smallest
+    // weight below a bound) then form a prefix, located with nz_lt
+    if (nzc > 1) {
+      uint64_t *kk0, *kk1;
+      TRY(tmp.alloc(&kk0, nzc));
+      TRY(tmp.alloc(&kk1, nzc));
+      k_nz_keys<<<grid_for(nzc), kThreads, 0, st>>>(g->nz, nzc, vbits, kk0);
+      bool alt = false;
+      TRY(radix_sort(kk0, nullptr, kk1, nullptr, nzc, vbits + wbits, hist_scratch, st, &alt));
+      k_nz_from_keys<<<grid_for(nzc), kThreads, 0, st>>>(alt ? kk1 : kk0, nzc, vbits, g->nz);
+      EIC_CUDA_TRY(cudaGetLastError());
+      EIC_CUDA_TRY(cudaStreamSynchronize(st));
+      tmp.release(kk0);
+      tmp.release(kk1);
+    }
+    nz_lt_len = (maxw < 65535u ? maxw + 1 : 65536u) + 1;
+    TRY(galloc(g, &g->nz_lt, nz_lt_len));
+    k_nz_lt<<<grid_for(nzc + 1), kThreads, 0, st>>>(g->nz, nzc, nz_lt_len, g->nz_lt);
     EIC_CUDA_TRY(cudaGetLastError());
   }
   EIC_CUDA_TRY(cudaMemcpyAsync(hs, small, sizeof(hs), cudaMemcpyDeviceToHost, st));
@@ -456,6 +510,8 @@ int build(eic_graph* g, const uint32_t* src, const uint32_t* dst, const uint32_t
   dg.rtow = g->rtow;
   dg.nz = g->nz;
   dg.nz_count = nzc;
+  dg.nz_lt = g->nz_lt;
+  dg.nz_lt_len = nz_lt_len;
   dg.maxw = maxw;
   dg.minw = minw;
   dg.max_deg = maxdeg;
@@ -538,8 +594,17 @@ int eic_graph_export(const eic_graph* g, uint64_t* row_ptr, uint32_t* nbr, uint3
   cudaSetDevice(g->device);
   int rc = EIC_OK;
   const uint64_t E = g->dg.two_m;
-  if (row_ptr && cudaMemcpy(row_ptr, g->row, ((uint64_t)g->dg.n + 1) * 8, cudaMemcpyDeviceToHost) != cudaSuccess)
-    rc = EIC_ECUDA;
+  if (row_ptr) {
+    const uint64_t cnt = (uint64_t)g->dg.n + 1;
+    uint32_t* h = (uint32_t*)malloc(cnt * 4);
+    if (!h) {
+      rc = EIC_ENOMEM;
+    } else {
+      if (cudaMemcpy(h, g->row, cnt * 4, cudaMemcpyDeviceToHost) != cudaSuccess) rc = EIC_ECUDA;
+      for (uint64_t i = 0; rc == EIC_OK && i < cnt; ++i) row_ptr[i] = h[i];
+      free(h);
+    }
+  }
   if ((nbr || w) && E > 0 && rc == EIC_OK) {
     uint2* h = (uint2*)malloc(E * sizeof(uint2));
     if (!h) {

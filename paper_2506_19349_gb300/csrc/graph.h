@@ -5,13 +5,13 @@
 
 #include "common.cuh"
 
-struct HeavyItem {
-  uint64_t beg;     // first adjacency index of the window
-  uint64_t prefix;  // entries of all earlier heavy items in this round
-  uint32_t u;       // vertex whose row is read
-  uint32_t d;       // its distance (push) or current distance (pull)
-  uint32_t mode;    // 0 push, 2 pull
-  uint32_t pad;
+// A window of at most kTaskLen adjacency entries relaxed by one warp in a
+// round's task phase.
+struct Task {
+  uint32_t beg;  // first adjacency index
+  uint32_t len;  // entries, <= 64
+  uint32_t u;    // the vertex whose row is read
+  uint32_t d;    // its distance (push); 0xFFFFFFFF marks a pull request
 };
 
 // Control block shared by the blocks of the persistent kernel.
@@ -20,23 +20,22 @@ struct Ctl {
   int64_t lb, ub, st, lb0;
   uint32_t step, done;
   uint32_t push_beg, push_end;  // settled-list range pushed in round 1
-  uint32_t pull_on, pull_src, pull_cnt, extra_s;
+  uint32_t pull_on, pull_cnt, extra_s;
   uint32_t step_off_cur;  // settled-list offset where the current step's vertices start
-  uint32_t ul_out;        // unsettled list written by this step's pull (0 or 1)
   // private to the step-boundary block
   int64_t st0, st1, gap_lb;
   uint64_t sumd_lb, highd_lb;
   int64_t max_settled;
-  uint32_t ul_sel, ul_valid;
   uint32_t rounds_in_step;
   uint32_t trace_len;
+  uint32_t tl_len;  // diagnostic timeline events recorded
   // appended with atomics during phases
   uint32_t qcnt[3];
+  uint32_t work[3];  // dynamic chunk counters, by round id mod 3
   uint32_t settled_cnt;
   uint32_t touched_cnt;
-  uint32_t ulcnt[2];
   uint32_t ub_cand;
-  unsigned long long heavy_packed[3];  // (items << 40) | entries, by round id mod 3
+  uint32_t tcnt[3];  // tasks of the round, by round id mod 3
   uint32_t s2_done;
   uint32_t acc_maxd;
   unsigned long long acc_deg;
@@ -51,19 +50,23 @@ struct Workspace {
   uint32_t n = 0;
   uint32_t* stamp = nullptr;
   uint32_t* q[2] = {nullptr, nullptr};
-  uint32_t* settled = nullptr;
+  uint32_t* sid = nullptr;   // settled list: vertex
+  uint32_t* sd = nullptr;    // settled list: final distance
+  uint32_t* scur = nullptr;  // settled list: window cursor (offset in the row)
+  uint32_t* cursor = nullptr;
   uint32_t* touched = nullptr;
-  uint32_t* ul[2] = {nullptr, nullptr};
+  uint32_t* sbits = nullptr;  // settled bitmap
   uint32_t* hist = nullptr;
   unsigned long long* ring = nullptr;
-  HeavyItem* heavy = nullptr;
+  Task* tasks = nullptr;
   int64_t* step_ub = nullptr;
   uint32_t* step_off = nullptr;
   eic_step* trace = nullptr;
+  unsigned long long* timeline = nullptr;
   Ctl* ctl = nullptr;
   Ctl* ctl_host = nullptr;  // pinned mirror for status readback
   uint32_t ring_bits = 0, ring_shift = 0;
-  uint32_t heavy_cap = 0, step_cap = 0;
+  uint32_t task_cap = 0, step_cap = 0;
   uint64_t bytes = 0;
   uint32_t host_round_base = 0;
   int grid = 0, block = 0;  // cached cooperative launch shape
@@ -72,13 +75,14 @@ struct Workspace {
 struct eic_graph {
   int device = 0;
   DevGraph dg{};
-  uint64_t* row = nullptr;
+  uint32_t* row = nullptr;
   uint2* adj = nullptr;
   uint32_t* drank = nullptr;
   uint32_t* dvals = nullptr;
   uint32_t* dcnt0 = nullptr;
   uint32_t* rtow = nullptr;
-  uint32_t* nz = nullptr;
+  uint2* nz = nullptr;
+  uint32_t* nz_lt = nullptr;
   uint64_t bytes = 0;
   Workspace ws;
   std::mutex mu;

@@ -7,20 +7,26 @@
 // Device layout per query (workspace, reused across queries of one graph):
 //   dist[n]      caller's buffer, u32, +inf = 0xFFFFFFFF, updated by atomicMin
 //   stamp[n]     round id of the last frontier insertion (the SAP of Algorithm 1)
+//   cursor[n]    where the last window relaxed from a vertex ended (offset in its row)
 //   q[2][n]      frontier queues, one per round parity
-//   settled[n]   vertices in settling order; step k owns [step_off[k], step_off[k+1])
+//   sid/sd/scur  settled list in settling order (vertex, final distance, window
+//                cursor); step k owns [step_off[k], step_off[k+1])
 //   touched[n]   first-step insertions (the first step's ub shrinks, so its
 //                tentative distances >= the final ub are reset to +inf)
-//   ul[2][n]     compacted unsettled lists for the pull of Function 1
+//   sbits[n/32]  settled bitmap: the pull set of Function 1 is the unsettled part of
+//                a prefix of the non-isolated vertices ordered by smallest row weight
 //   hist[D]      unsettled vertices per distinct degree (for highD)
 //   ring[R]      degree sums of settled vertices by distance mod R (for the
 //                sumD differences of Function 2's candidates)
-//   heavy[]      long windows spread over the whole grid
+//   tasks[]      windows longer than heavy_min, cut into 64-entry tasks for the grid
 //
-// Phases (one grid barrier each): a round over the frontier (the first round
-// of a step also runs Function 1's push set and pull), an optional heavy
-// phase, and per step one statistics pass whose last block evaluates
-// Eq. 1-3 and Function 2 and publishes the next <st, lb, ub>.
+// Phases (one grid barrier each): a round (the first round of a step runs
+// Function 1's push set and pull), an optional task phase, and per step one
+// statistics pass whose last block evaluates Eq. 1-3 and Function 2 and
+// publishes the next <st, lb, ub>. A round hands out chunks of blockDim items
+// to blocks (the first statically, then by an atomic counter); a block finds
+// each item's window in the weight-sorted row and relaxes the concatenation of
+// its chunk's windows with all its threads.
 #include <stdlib.h>
 #include <string.h>
 
@@ -31,28 +37,27 @@ using namespace eic;
 
 namespace {
 
-constexpr uint32_t kModePush = 0;     // frontier vertex: relax its window
-constexpr uint32_t kModePushSet = 1;  // settled vertex of Function 1's push set
+constexpr uint32_t kModePush = 0;     // frontier or push-set vertex: relax its window
 constexpr uint32_t kModePull = 2;     // unsettled vertex pulling over its light prefix
-constexpr int kMaxWarps = 32;
+constexpr uint32_t kNone = 0xFFFFFFFFu;
 constexpr int kShRanks = 1024;
 constexpr int kShRing = 2048;
-constexpr uint64_t kMask40 = (1ull << 40) - 1;
-constexpr uint32_t kHeavyChunk = 256;
 
 struct KArgs {
   DevGraph G;
   uint32_t* dist;
   uint32_t* stamp;
+  uint32_t* cursor;
   uint32_t* q0;
   uint32_t* q1;
-  uint32_t* settled;
+  uint32_t* sid;
+  uint32_t* sd;
+  uint32_t* scur;
   uint32_t* touched;
-  uint32_t* ul0;
-  uint32_t* ul1;
+  uint32_t* sbits;  // settled bitmap
   uint32_t* hist;
   unsigned long long* ring;
-  HeavyItem* heavy;
+  Task* tasks;
   int64_t* step_ub;
   uint32_t* step_off;
   eic_step* trace;
@@ -67,16 +72,37 @@ struct KArgs {
   uint64_t max_spin;
   uint32_t flags;
   uint32_t ring_mask, ring_shift;
-  uint32_t heavy_cap, step_cap, trace_cap;
+  uint32_t task_cap, step_cap, trace_cap;
+  unsigned long long* timeline;  // NULL unless the caller asked for it
+  uint32_t timeline_cap;
 };
 
-struct WarpScr {
-  unsigned long long beg[32];
+constexpr uint32_t kMaxBlock = 512;
+constexpr uint32_t kMaxWarps = kMaxBlock / 32;
+constexpr uint32_t kTaskLen = 64;     // adjacency entries per grid task
+constexpr uint32_t kStageT = 1024;    // tasks staged per block
+constexpr uint32_t kStageQ = 4096;    // next-frontier appends staged per block
+constexpr uint32_t kStageF = 4096;    // settled-list appends staged per block
+
+struct WarpScr {  // one warp's small windows
+  uint32_t beg[32];
   uint32_t excl[32];
+  uint32_t val[32];  // source distance (push) or best candidate (pull)
   uint32_t u[32];
-  uint32_t d[32];
-  uint32_t best[32];
   uint32_t mode[32];
+};
+
+struct RoundScr {
+  WarpScr w[kMaxWarps];
+};
+
+// Appends of a block gathered in shared memory and written with one global
+// atomic per list and round; what does not fit goes out warp by warp.
+struct Stage {
+  uint32_t qn, fn, tn, qbase, fbase, tbase;
+  uint32_t qbuf[kStageQ];
+  uint32_t fbuf[kStageF];
+  Task tbuf[kStageT];
 };
 
 struct S2Scr {
@@ -85,13 +111,13 @@ struct S2Scr {
 };
 
 struct S3Scr {
-  unsigned long long part[1024];
+  unsigned long long part[kMaxBlock];
   double bp[32];
   uint32_t bk[32];
 };
 
 union PhaseScr {
-  WarpScr w[kMaxWarps];
+  RoundScr r;
   S2Scr s2;
   S3Scr s3;
 };
@@ -99,32 +125,84 @@ union PhaseScr {
 // Control values every block holds between barriers.
 struct Local {
   int64_t lb, ub, st, lb0;
-  uint32_t step, rid, qsel, cur_cnt, rin;
-  uint32_t push_beg, push_end, pull_on, pull_src, pull_cnt, extra_s, step_off_cur, ul_out;
+  uint32_t step, rid, qsel, cur_cnt;
+  uint32_t push_beg, push_end, pull_on, pull_cnt, extra_s, step_off_cur, done;
+};
+
+// State of the step controller, kept in block 0's shared memory across steps.
+struct BState {
+  int64_t st0, st1, gap_lb, max_settled;
+  uint64_t sumd_lb, highd_lb;
+  uint32_t j0;
 };
 
 struct Counters {
   unsigned long long frontier, trav, pulls, improved, heavy;
 };
 
-template <typename T>
-__device__ __forceinline__ T vload(const T* p) {
-  return *(const volatile T*)p;
+__device__ __forceinline__ void tl_mark(const KArgs& A, uint32_t kind, uint32_t rid) {
+  if (!A.timeline) return;
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  uint32_t i = atomicAdd(&A.ctl->tl_len, 1u);
+  if (i < A.timeline_cap) {
+    A.timeline[2 * i] = t;
+    A.timeline[2 * i + 1] = ((unsigned long long)kind << 32) | rid;
+  }
+}
+
+constexpr uint32_t kFlagBlockTimeline = 1u << 30;  // diagnostic: per-block phase marks
+
+// per-block mark: kind 6 item phase done, 7 task phase done (tag has the block id)
+__device__ __forceinline__ void tl_block(const KArgs& A, uint32_t kind, uint32_t rid) {
+  if (!A.timeline || !(A.flags & kFlagBlockTimeline) || threadIdx.x != 0) return;
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  uint32_t i = atomicAdd(&A.ctl->tl_len, 1u);
+  if (i < A.timeline_cap) {
+    A.timeline[2 * i] = t;
+    A.timeline[2 * i + 1] = ((unsigned long long)kind << 32) | ((unsigned long long)blockIdx.x << 48) | rid;
+  }
 }
 
 __device__ __forceinline__ int64_t d64(uint32_t d) { return d == EIC_INF ? EIC_INF_T : (int64_t)d; }
 
 // first index in [b, e) of the weight-sorted row with weight >= t
-__device__ __forceinline__ uint64_t lower_bound_w(const uint2* __restrict__ adj, uint64_t b, uint64_t e, int64_t t) {
+__device__ __forceinline__ uint32_t lower_bound_w(const uint2* __restrict__ adj, uint32_t b, uint32_t e, int64_t t) {
   if (t <= 1) return b;  // weights are >= 1
   while (b < e) {
-    uint64_t mid = b + ((e - b) >> 1);
+    uint32_t mid = b + ((e - b) >> 1);
     if ((int64_t)__ldg(&adj[mid].y) < t)
       b = mid + 1;
     else
       e = mid;
   }
   return b;
+}
+
+// The same, given that every entry before p has weight < t: exponential
+// probes forward from p, then a binary search in the last interval. Costs
+// O(log distance), and a short window costs one or two probes of one sector.
+__device__ __forceinline__ uint32_t gallop_w(const uint2* __restrict__ adj, uint32_t p, uint32_t e, int64_t t) {
+  if (t <= 1 || p >= e) return p;
+  if ((int64_t)__ldg(&adj[p].y) >= t) return p;
+  uint32_t lo = p;  // weight at lo < t
+  uint32_t hi;
+  uint64_t step = 1;
+  for (;;) {
+    const uint64_t h = (uint64_t)lo + step;
+    if (h >= e) {
+      hi = e;
+      break;
+    }
+    if ((int64_t)__ldg(&adj[h].y) >= t) {
+      hi = (uint32_t)h;
+      break;
+    }
+    lo = (uint32_t)h;
+    step <<= 1;
+  }
+  return lower_bound_w(adj, lo + 1, hi, t);
 }
 
 struct RoundCtx {
@@ -135,228 +213,277 @@ struct RoundCtx {
   uint32_t* qcnt_out;
   uint32_t* first_list;
   uint32_t* first_cnt;
-  uint32_t* ul_out;
-  uint32_t* ulcnt_out;
-  unsigned long long* heavy_ctr;
+  uint32_t* tcnt;
+  uint32_t* work;
 };
+
+// Warp-collective append of v for the lanes with want: into the block's
+// shared stage while it has room, else straight to the global list.
+template <typename T>
+__device__ __forceinline__ void staged_append(bool want, T v, uint32_t* sn, T* sbuf, uint32_t cap, uint32_t* gcnt,
+                                              T* glist) {
+  const uint32_t mask = __ballot_sync(EIC_FULL_MASK, want);
+  if (mask == 0) return;
+  const uint32_t lane = lane_id(), leader = __ffs(mask) - 1;
+  uint32_t base = 0;
+  if (lane == leader) base = atomicAdd(sn, (uint32_t)__popc(mask));
+  base = __shfl_sync(EIC_FULL_MASK, base, leader);
+  const uint32_t pos = base + __popc(mask & ((1u << lane) - 1u));
+  const bool spill = want && pos >= cap;
+  if (want && !spill) sbuf[pos] = v;
+  const uint32_t slot = warp_append(spill, gcnt);
+  if (spill) __stcg(&glist[slot], v);
+}
+
+// Flush the block's stages to the global lists (block-uniform call).
+__device__ __forceinline__ void stage_flush(Stage& T, const RoundCtx& R, Task* tasks) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const uint32_t qn = min(T.qn, kStageQ), fn = min(T.fn, kStageF), tn = min(T.tn, kStageT);
+    T.qn = qn;
+    T.fn = fn;
+    T.tn = tn;
+    T.qbase = qn ? atomicAdd(R.qcnt_out, qn) : 0;
+    T.fbase = fn ? atomicAdd(R.first_cnt, fn) : 0;
+    T.tbase = tn ? atomicAdd(R.tcnt, tn) : 0;
+  }
+  __syncthreads();
+  for (uint32_t i = threadIdx.x; i < T.qn; i += blockDim.x) __stcg(&R.qout[T.qbase + i], T.qbuf[i]);
+  for (uint32_t i = threadIdx.x; i < T.fn; i += blockDim.x) __stcg(&R.first_list[T.fbase + i], T.fbuf[i]);
+  for (uint32_t i = threadIdx.x; i < T.tn; i += blockDim.x) tasks[T.tbase + i] = T.tbuf[i];
+  __syncthreads();
+  if (threadIdx.x == 0) T.qn = T.fn = T.tn = 0;
+}
+
+// Cut the window [b, b + len) of vertex u into kTaskLen-entry tasks, staged in
+// the block (or written straight to the global list when the stage is full).
+__device__ __forceinline__ void emit_tasks(const KArgs& A, const RoundCtx& R, Stage& T, uint32_t b, uint32_t len,
+                                           uint32_t u, uint32_t d) {
+  const uint32_t nt = (len + kTaskLen - 1) / kTaskLen;
+  const uint32_t pos = atomicAdd(&T.tn, nt);
+  const uint32_t in_stage = pos < kStageT ? min(nt, kStageT - pos) : 0;
+  // the rest goes straight to the global list; capacity covers 2m / 16 tasks per round
+  const uint32_t gpos = nt > in_stage ? atomicAdd(R.tcnt, nt - in_stage) : 0;
+  for (uint32_t k = 0; k < nt; ++k) {
+    Task t;
+    t.beg = b + k * kTaskLen;
+    t.len = min(kTaskLen, len - k * kTaskLen);
+    t.u = u;
+    t.d = d;
+    if (k < in_stage)
+      T.tbuf[pos + k] = t;
+    else
+      A.tasks[gpos + (k - in_stage)] = t;
+  }
+}
 
 // Successful relaxation of v to nd (old = previous distance): SAP into the
 // next frontier, first insertion into the settled (or first-step) list, and
 // in the first step the running min over high-degree vertices that becomes
-// ub (Algorithm 1). Warp-collective: every lane calls it.
+// ub (Algorithm 1). Warp-collective: every lane calls it. With a stage the
+// appends go through shared memory.
 __device__ __forceinline__ void on_success(const KArgs& A, const RoundCtx& R, bool ok, uint32_t v, uint32_t nd,
-                                           uint32_t old, Counters& C) {
-  bool sap = ok && (atomicExch(&A.stamp[v], R.rid) != R.rid);
-  uint32_t slot = warp_append(sap, R.qcnt_out);
-  if (sap) __stcg(&R.qout[slot], v);
-  bool first = ok && old == EIC_INF;
-  uint32_t slot2 = warp_append(first, R.first_cnt);
-  if (first) __stcg(&R.first_list[slot2], v);
+                                           uint32_t old, Counters& C, Stage* T = nullptr) {
+  const bool sap = ok && (atomicExch(&A.stamp[v], R.rid) != R.rid);
+  const bool first = ok && old == EIC_INF;
+  if (T) {
+    staged_append(sap, v, &T->qn, T->qbuf, kStageQ, R.qcnt_out, R.qout);
+    staged_append(first, v, &T->fn, T->fbuf, kStageF, R.first_cnt, R.first_list);
+  } else {
+    const uint32_t slot = warp_append(sap, R.qcnt_out);
+    if (sap) __stcg(&R.qout[slot], v);
+    const uint32_t slot2 = warp_append(first, R.first_cnt);
+    if (first) __stcg(&R.first_list[slot2], v);
+  }
   if (R.step1 && ok) {
-    uint64_t dg = __ldg(&A.G.row[v + 1]) - __ldg(&A.G.row[v]);
+    const uint32_t dg = __ldg(&A.G.row[v + 1]) - __ldg(&A.G.row[v]);
     if (dg >= A.G.highd0) atomicMin(&A.ctl->ub_cand, nd);
   }
   C.improved += ok ? 1 : 0;
 }
 
-// One warp, up to 32 items: windows by binary search in the weight-sorted
-// rows, long windows handed to the heavy list, the rest relaxed cooperatively
-// over the concatenation of the warp's windows.
-__device__ void process_items(const KArgs& A, const RoundCtx& R, WarpScr& S, const Local& L, uint32_t base,
-                              uint32_t nitems, bool round1, const uint32_t* qin, const uint32_t* pull_list,
-                              Counters& C) {
-  const uint32_t lane = lane_id();
-  const uint32_t i = base + lane;
-  const bool valid = i < nitems;
-  uint32_t mode = kModePush, u = 0;
-  if (valid) {
-    if (!round1) {
-      u = __ldcg(&qin[i]);
-    } else {
-      uint32_t np = L.push_end - L.push_beg;
-      if (i < np) {
-        u = __ldcg(&A.settled[L.push_beg + i]);
-        mode = kModePushSet;
-      } else if (i < np + L.pull_cnt) {
-        u = __ldcg(&pull_list[i - np]);
+// One round over nitems items. Items are frontier vertices (queue qin), or in
+// a step's first round Function 1's push set (a settled-list range), its pull
+// set (a prefix of the weight-ordered non-isolated vertices) and, once, the
+// source. Warp by warp without block synchronisation, each lane finds its
+// item's window in the weight-sorted row; windows up to heavy_min entries are
+// relaxed by the warp over their concatenation, longer ones become grid tasks.
+// A pull reads the prefix of its vertex's row with weight < ub - st.
+// List appends are staged in shared memory and flushed once per block.
+__device__ void round_phase(const KArgs& A, const RoundCtx& R, const Local& L, RoundScr& S, Stage& T,
+                            uint32_t nitems, bool round1, const uint32_t* qin, Counters& C) {
+  const uint32_t tid = threadIdx.x, nt = blockDim.x, lane = lane_id(), warp = tid >> 5;
+  const uint32_t np = round1 ? L.push_end - L.push_beg : 0;
+  const uint32_t npp = np + L.pull_cnt;
+  const uint32_t gwarp = blockIdx.x * (nt >> 5) + warp, nwarps = gridDim.x * (nt >> 5);
+  const int64_t pull_bound = R.ub - R.st;
+  WarpScr& W = S.w[warp];
+  for (uint32_t base = gwarp * 32; base < nitems; base += nwarps * 32) {
+    const uint32_t i = base + lane;
+    uint32_t u = 0, val = EIC_INF, b = 0, len = 0, mode = kModePush;
+    if (i < nitems) {
+      if (!round1 || i >= npp) {  // frontier vertex (or the source, once)
+        u = round1 ? A.s : __ldcg(&qin[i]);
+        const uint32_t d = __ldcg(&A.dist[u]);
+        const uint32_t rb = __ldg(&A.G.row[u]), re = __ldg(&A.G.row[u + 1]);
+        val = d;
+        if (d != EIC_INF && !(d > 0 && re - rb == 1)) {  // Paths excludes leaves (Algorithm 1)
+          C.frontier += 1;
+          const int64_t hi = R.ub_eff - (int64_t)d;
+          if (hi > 0) {
+            b = lower_bound_w(A.G.adj, rb, re, R.lb - (int64_t)d);
+            const uint32_t e = gallop_w(A.G.adj, b, re, hi);
+            __stcg(&A.cursor[u], e - rb);
+            len = e - b;
+          }
+        }
+      } else if (i < np) {  // push set: settled, lb0 <= dist <= st
+        const uint32_t idx = L.push_beg + i;
+        u = __ldcg(&A.sid[idx]);
+        const uint32_t d = __ldcg(&A.sd[idx]);
+        val = d;
+        if ((int64_t)d >= R.lb0 && (int64_t)d <= R.st) {
+          const uint32_t rb = __ldg(&A.G.row[u]), re = __ldg(&A.G.row[u + 1]);
+          if (!(d > 0 && re - rb == 1)) {
+            C.frontier += 1;
+            const uint32_t cur = __ldcg(&A.scur[idx]);
+            // windows of consecutive steps are contiguous: resume at the cursor
+            b = cur == kNone ? lower_bound_w(A.G.adj, rb, re, R.lb - (int64_t)d)
+                             : gallop_w(A.G.adj, rb + cur, re, R.lb - (int64_t)d);
+            const uint32_t e = gallop_w(A.G.adj, b, re, R.ub_eff - (int64_t)d);
+            __stcg(&A.scur[idx], e - rb);
+            len = e - b;
+          }
+        }
+      } else {  // pull set: unsettled, smallest weight < ub - st (Function 1)
+        u = __ldg(&A.G.nz[i - np].x);
         mode = kModePull;
-      } else {
-        u = A.s;
-      }
-    }
-  }
-  uint32_t d = valid ? __ldcg(&A.dist[u]) : EIC_INF;
-  uint64_t b = 0, e = 0;
-  bool keep_ul = false, counted = false;
-  if (valid) {
-    const uint64_t rb = __ldg(&A.G.row[u]), re = __ldg(&A.G.row[u + 1]);
-    if (mode == kModePull) {
-      int64_t dd = d64(d);
-      if (dd >= R.lb) {
-        keep_ul = true;
-        if (dd > R.lb) {
-          b = rb;
-          e = lower_bound_w(A.G.adj, rb, re, R.ub - R.st);
-        }
-      }
-    } else {
-      bool skip = d == EIC_INF || (mode == kModePushSet && ((int64_t)d < R.lb0 || (int64_t)d > R.st)) ||
-                  (d > 0 && re - rb == 1);  // Paths excludes leaves (Algorithm 1)
-      if (!skip) {
-        counted = true;
-        int64_t hi = R.ub_eff - (int64_t)d;
-        if (hi > 0) {
-          b = lower_bound_w(A.G.adj, rb, re, R.lb - (int64_t)d);
-          e = lower_bound_w(A.G.adj, b, re, hi);
+        const uint32_t bits = __ldcg(&A.sbits[u >> 5]);
+        if (!((bits >> (u & 31)) & 1u)) {
+          // the row's first weight is below the bound (nz order): gallop from the second
+          b = __ldg(&A.G.row[u]);
+          len = gallop_w(A.G.adj, b + 1, __ldg(&A.G.row[u + 1]), pull_bound) - b;
         }
       }
     }
-  }
-  C.frontier += counted ? 1 : 0;
-  uint32_t us = warp_append(keep_ul, R.ulcnt_out);
-  if (keep_ul) __stcg(&R.ul_out[us], u);
-  uint64_t len = e - b;
-  if (mode == kModePull) C.pulls += len;
-  C.trav += len;
-  if (len > A.heavy_min) {
-    unsigned long long old = atomicAdd(R.heavy_ctr, (1ull << 40) | len);
-    uint32_t idx = (uint32_t)(old >> 40);
-    HeavyItem h;
-    h.beg = b;
-    h.prefix = old & kMask40;
-    h.u = u;
-    h.d = d;
-    h.mode = mode == kModePull ? kModePull : kModePush;
-    h.pad = 0;
-    A.heavy[idx] = h;  // capacity covers 2m / heavy_min items per round
-    C.heavy += 1;
-    len = 0;
-  }
-  const uint32_t len32 = (uint32_t)len;
-  const uint32_t incl = warp_incl_scan(len32);
-  const uint32_t total = __shfl_sync(EIC_FULL_MASK, incl, 31);
-  S.beg[lane] = b;
-  S.excl[lane] = incl - len32;
-  S.u[lane] = u;
-  S.d[lane] = d;
-  S.mode[lane] = mode;
-  S.best[lane] = EIC_INF;
-  __syncwarp();
-  for (uint32_t g0 = 0; g0 < total; g0 += 32) {
-    const uint32_t g = g0 + lane;
-    const bool act = g < total;
-    bool ok = false;
-    uint32_t v = 0, nd = 0, old = 0;
-    if (act) {
-      uint32_t lo = 0, hi = 31;
-      while (lo < hi) {  // last lane whose window starts at or before g
-        uint32_t mid = (lo + hi + 1) >> 1;
-        if (S.excl[mid] <= g)
-          lo = mid;
-        else
-          hi = mid - 1;
-      }
-      const uint2 ent = __ldg(&A.G.adj[S.beg[lo] + (g - S.excl[lo])]);
-      v = ent.x;
-      const uint32_t dv = __ldcg(&A.dist[v]);
-      if (S.mode[lo] != kModePull) {
-        nd = S.d[lo] + ent.y;  // inside [lb, min(ub, 2^32-1)) by the window bounds
-        if (nd < dv) {
-          old = atomicMin(&A.dist[v], nd);
-          ok = nd < old;
-        }
-      } else if (dv != EIC_INF) {
-        const int64_t dvv = dv;
-        if (dvv >= R.st && dvv < R.lb && dvv + ent.y < R.ub) atomicMin(&S.best[lo], (uint32_t)(dvv + ent.y));
-      }
+    if (len > A.heavy_min) {
+      emit_tasks(A, R, T, b, len, u, mode == kModePull ? kNone : val);
+      C.heavy += (len + kTaskLen - 1) / kTaskLen;
+      len = 0;
     }
-    on_success(A, R, ok, v, nd, old, C);
-  }
-  __syncwarp();
-  bool pok = false;
-  uint32_t pold = 0;
-  const uint32_t pbest = S.best[lane];
-  if (valid && mode == kModePull && pbest < d) {
-    pold = atomicMin(&A.dist[u], pbest);
-    pok = pbest < pold;
-  }
-  on_success(A, R, pok, u, pbest, pold, C);
-  __syncwarp();
-}
-
-// Heavy windows of this round, 256 entries per warp task over the grid.
-__device__ void heavy_phase(const KArgs& A, const RoundCtx& R, unsigned long long packed, Counters& C) {
-  const uint32_t cnt = (uint32_t)(packed >> 40);
-  const uint64_t total = packed & kMask40;
-  const uint32_t lane = lane_id();
-  const uint32_t wpb = blockDim.x >> 5;
-  const uint64_t nwarps = (uint64_t)gridDim.x * wpb;
-  const uint64_t nch = (total + kHeavyChunk - 1) / kHeavyChunk;
-  for (uint64_t c = (uint64_t)blockIdx.x * wpb + (threadIdx.x >> 5); c < nch; c += nwarps) {
-    const uint64_t e0 = c * kHeavyChunk, e1 = e0 + kHeavyChunk < total ? e0 + kHeavyChunk : total;
-    uint32_t j = 0;
-    if (lane == 0) {
-      uint32_t lo = 0, hi = cnt - 1;
-      while (lo < hi) {
-        uint32_t mid = (lo + hi + 1) >> 1;
-        if (__ldcg(&A.heavy[mid].prefix) <= e0)
-          lo = mid;
-        else
-          hi = mid - 1;
-      }
-      j = lo;
-    }
-    j = __shfl_sync(EIC_FULL_MASK, j, 0);
-    for (uint64_t g0 = e0; g0 < e1; g0 += 32) {
-      const uint64_t g = g0 + lane;
-      const bool act = g < e1;
+    const uint32_t incl = warp_incl_scan(len);
+    const uint32_t total = __shfl_sync(EIC_FULL_MASK, incl, 31);
+    W.beg[lane] = b;
+    W.excl[lane] = incl - len;
+    W.val[lane] = mode == kModePull ? EIC_INF : val;
+    W.u[lane] = u;
+    W.mode[lane] = mode;
+    __syncwarp();
+    for (uint32_t g0 = 0; g0 < total; g0 += 32) {
+      const uint32_t g = g0 + lane;
       bool ok = false;
       uint32_t v = 0, nd = 0, old = 0;
-      if (act) {
-        uint32_t jj = j;
-        while (jj + 1 < cnt && __ldcg(&A.heavy[jj + 1].prefix) <= g) ++jj;
-        const uint64_t hb = __ldcg(&A.heavy[jj].beg), hp = __ldcg(&A.heavy[jj].prefix);
-        const uint32_t hu = __ldcg(&A.heavy[jj].u), hd = __ldcg(&A.heavy[jj].d), hm = __ldcg(&A.heavy[jj].mode);
-        const uint2 ent = __ldg(&A.G.adj[hb + (g - hp)]);
-        const uint32_t dv = __ldcg(&A.dist[ent.x]);
-        if (hm != kModePull) {
-          v = ent.x;
-          nd = hd + ent.y;
+      if (g < total) {
+        uint32_t lo = 0, hi = 31;
+        while (lo < hi) {  // last lane whose window starts at or before g
+          const uint32_t mid = (lo + hi + 1) >> 1;
+          if (W.excl[mid] <= g)
+            lo = mid;
+          else
+            hi = mid - 1;
+        }
+        const uint2 ent = __ldg(&A.G.adj[W.beg[lo] + (g - W.excl[lo])]);
+        v = ent.x;
+        if (W.mode[lo] != kModePull) {
+          C.trav += 1;
+          nd = W.val[lo] + ent.y;  // inside [lb, min(ub, 2^32-1)) by the window bounds
+          const uint32_t dv = __ldcg(&A.dist[v]);
           if (nd < dv) {
             old = atomicMin(&A.dist[v], nd);
             ok = nd < old;
           }
-        } else if (dv != EIC_INF) {
+        } else if ((int64_t)ent.y < pull_bound) {  // request answered by a settled v with st <= dist[v] < lb
+          C.trav += 1;
+          C.pulls += 1;
+          const uint32_t dv = __ldcg(&A.dist[v]);
           const int64_t dvv = dv;
-          if (dvv >= R.st && dvv < R.lb && dvv + ent.y < R.ub) {
-            v = hu;
-            nd = (uint32_t)(dvv + ent.y);
+          if (dv != EIC_INF && dvv >= R.st && dvv < R.lb && dvv + ent.y < R.ub)
+            atomicMin(&W.val[lo], (uint32_t)(dvv + ent.y));
+        }
+      }
+      on_success(A, R, ok, v, nd, old, C, &T);
+    }
+    __syncwarp();
+    bool pok = false;
+    uint32_t pold = 0;
+    const uint32_t pbest = W.val[lane];
+    if (mode == kModePull && pbest != EIC_INF) {
+      pold = atomicMin(&A.dist[u], pbest);
+      pok = pbest < pold;
+    }
+    on_success(A, R, pok, u, pbest, pold, C, &T);
+    __syncwarp();
+  }
+  tl_block(A, 6, R.rid);
+  stage_flush(T, R, A.tasks);
+}
+
+// The round's tasks, one warp per task of at most 64 entries.
+__device__ void task_phase(const KArgs& A, const RoundCtx& R, uint32_t ntasks, Stage& T, Counters& C) {
+  const uint32_t lane = lane_id();
+  const uint32_t wpb = blockDim.x >> 5;
+  const uint32_t nwarps = gridDim.x * wpb;
+  const int64_t pull_bound = R.ub - R.st;
+  for (uint32_t t = blockIdx.x * wpb + (threadIdx.x >> 5); t < ntasks; t += nwarps) {
+    const Task tk = A.tasks[t];
+    if (tk.d != kNone) {  // push
+#pragma unroll
+      for (uint32_t h = 0; h < 2; ++h) {
+        const uint32_t j = lane + 32 * h;
+        bool ok = false;
+        uint32_t v = 0, nd = 0, old = 0;
+        if (j < tk.len) {
+          const uint2 ent = __ldg(&A.G.adj[tk.beg + j]);
+          v = ent.x;
+          nd = tk.d + ent.y;
+          C.trav += 1;
+          const uint32_t dv = __ldcg(&A.dist[v]);
+          if (nd < dv) {
             old = atomicMin(&A.dist[v], nd);
             ok = nd < old;
           }
         }
+        on_success(A, R, ok, v, nd, old, C, &T);
       }
-      on_success(A, R, ok, v, nd, old, C);
+    } else {  // pull request over a row segment
+      uint32_t best = EIC_INF;
+#pragma unroll
+      for (uint32_t h = 0; h < 2; ++h) {
+        const uint32_t j = lane + 32 * h;
+        if (j < tk.len) {
+          const uint2 ent = __ldg(&A.G.adj[tk.beg + j]);
+          if ((int64_t)ent.y < pull_bound) {
+            C.trav += 1;
+            C.pulls += 1;
+            const uint32_t dv = __ldcg(&A.dist[ent.x]);
+            const int64_t dvv = dv;
+            if (dv != EIC_INF && dvv >= R.st && dvv < R.lb && dvv + ent.y < R.ub)
+              best = min(best, (uint32_t)(dvv + ent.y));
+          }
+        }
+      }
+      for (int o = 16; o > 0; o >>= 1) best = min(best, __shfl_xor_sync(EIC_FULL_MASK, best, o));
+      bool ok = false;
+      uint32_t old = 0;
+      if (lane == 0 && best != EIC_INF) {
+        old = atomicMin(&A.dist[tk.u], best);
+        ok = best < old;
+      }
+      on_success(A, R, ok, tk.u, best, old, C, &T);
     }
   }
-}
-
-__device__ __forceinline__ unsigned long long block_sum_u64(unsigned long long x, unsigned long long* sh) {
-  x = warp_sum_u64(x);
-  __syncthreads();
-  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = x;
-  __syncthreads();
-  unsigned long long t = 0;
-  if (threadIdx.x < 32) {
-    t = threadIdx.x < (blockDim.x >> 5) ? sh[threadIdx.x] : 0;
-    t = warp_sum_u64(t);
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) sh[0] = t;
-  __syncthreads();
-  t = sh[0];
-  __syncthreads();
-  return t;
+  tl_block(A, 7, R.rid);
+  stage_flush(T, R, A.tasks);
 }
 
 // Function 2 for the boundary <lb, ub> -> next pair <ub, ub + gap(ub)>, run by
@@ -377,8 +504,7 @@ __device__ int64_t block_compute_st(const KArgs& A, S3Scr& S, int64_t ub, uint64
   for (uint64_t q = sl + t * cs; q < sl + (t + 1) * cs && q <= su; ++q) mine += __ldcg(&A.ring[q & A.ring_mask]);
   S.part[t] = mine;
   __syncthreads();
-  // suffix sums: part[t] <- sum over chunks after t
-  for (uint32_t o = 1; o < nt; o <<= 1) {
+  for (uint32_t o = 1; o < nt; o <<= 1) {  // suffix sums over chunks
     unsigned long long v = t + o < nt ? S.part[t + o] : 0;
     __syncthreads();
     S.part[t] += v;
@@ -390,6 +516,10 @@ __device__ int64_t block_compute_st(const KArgs& A, S3Scr& S, int64_t ub, uint64
     const int64_t x = st0 + (int64_t)(((uint64_t)k * (uint64_t)(st1 - st0)) / A.st_num);
     if (x >= ub) continue;
     const int64_t xc = x > ub - maxw ? x : ub - maxw;
+    if (k > 0) {  // the profit depends on x' only: the first candidate of each x' decides the argmax
+      const int64_t xp = st0 + (int64_t)(((uint64_t)(k - 1) * (uint64_t)(st1 - st0)) / A.st_num);
+      if ((xp > ub - maxw ? xp : ub - maxw) == xc) continue;
+    }
     const uint64_t q0 = (uint64_t)xc >> sh;
     const uint64_t c = (q0 - sl) / cs;
     unsigned long long dsum = c + 1 < nt ? S.part[c + 1] : 0;
@@ -434,11 +564,11 @@ __device__ int64_t block_compute_st(const KArgs& A, S3Scr& S, int64_t ub, uint64
   return st0 + (int64_t)(((uint64_t)k * (uint64_t)(st1 - st0)) / A.st_num);
 }
 
-// Step boundary, executed by the last block to finish the statistics pass:
-// sumD(ub), highD(ub), gap(ub) (Eq. 1-3), termination (Algorithm 1),
-// computeST (Function 2) and the push/pull sets of the next step's
-// Function 1. Publishes the new control values before the grid barrier.
-__device__ void step_boundary(const KArgs& A, PhaseScr& P, const Local& L, uint32_t rounds_in_step) {
+// Step boundary, executed by block 0 once every block finished the
+// statistics pass: sumD(ub), highD(ub), gap(ub) (Eq. 1-3), termination
+// (Algorithm 1), computeST (Function 2) and the push/pull sets of the next
+// step's Function 1. Publishes the new control values before the grid barrier.
+__device__ void step_boundary(const KArgs& A, PhaseScr& P, BState& B, const Local& L, uint32_t rounds_in_step) {
   Ctl* c = A.ctl;
   __shared__ int64_t sh_i[8];
   __shared__ uint64_t sh_u[4];
@@ -447,33 +577,29 @@ __device__ void step_boundary(const KArgs& A, PhaseScr& P, const Local& L, uint3
   const int64_t lb = L.lb, ub = L.ub;
   const uint32_t k = L.step;
   if (threadIdx.x == 0) {
-    const uint64_t settled_now = vload(&c->settled_cnt);
-    const uint64_t acc = vload(&c->acc_deg);
-    const uint64_t sumd_ub = vload(&c->sumd_lb) - acc;
+    const uint32_t settled_now = __ldcg(&c->settled_cnt);
+    const unsigned long long acc = __ldcg(&c->acc_deg);
+    const uint32_t acc_any = __ldcg(&c->acc_any), acc_maxd = __ldcg(&c->acc_maxd);
+    const uint64_t sumd_ub = B.sumd_lb - acc;
     sh_u[0] = sumd_ub;
     sh_u[1] = settled_now;
-    int64_t maxs = vload(&c->max_settled);
-    if (vload(&c->acc_any)) {
-      int64_t am = (int64_t)vload(&c->acc_maxd);
-      maxs = am > maxs ? am : maxs;
-    }
-    c->max_settled = maxs;
-    sh_i[0] = maxs;
-    // step table and trace row of step k
+    if (acc_any && (int64_t)acc_maxd > B.max_settled) B.max_settled = acc_maxd;
+    const int64_t maxs = B.max_settled;
     A.step_ub[k] = ub;
     if (k <= A.trace_cap && A.trace) {
       eic_step r;
       r.lb = lb;
       r.ub = ub;
       r.st = L.st;
-      r.gap_lb = vload(&c->gap_lb);
-      r.sumd_lb = vload(&c->sumd_lb);
-      r.highd_lb = vload(&c->highd_lb);
+      r.gap_lb = B.gap_lb;
+      r.sumd_lb = B.sumd_lb;
+      r.highd_lb = B.highd_lb;
       r.rounds = rounds_in_step;
       r.settled = settled_now - L.step_off_cur;
       A.trace[k - 1] = r;
     }
     c->trace_len = k;
+    c->cnt_rounds += rounds_in_step;
     // termination / overflow (Algorithm 1): max{finite dist} + maxW(G,1) < lb
     uint32_t done = 0;
     if (maxs + (int64_t)G.maxw >= (int64_t)EIC_INF) {
@@ -493,39 +619,26 @@ __device__ void step_boundary(const KArgs& A, PhaseScr& P, const Local& L, uint3
   if (sh_flag[0]) {
     if (threadIdx.x == 0) {
       c->done = 1;
+      c->s2_done = 0;
       __threadfence();
     }
     __syncthreads();
     return;
   }
-  int64_t gap_raw = 0, width = 0, st0 = 0, st1 = 0, gap_lb = 0;
   if (threadIdx.x == 0) {
-    gap_raw = dev_gap(sumd_ub, highd_ub, G.two_m, A.alpha, A.beta, G.rtow);
-    width = gap_raw << A.gap_shift;
-    st0 = k == 1 ? ub : vload(&c->st0);
-    st1 = vload(&c->st1);
-    if (st1 < 0 && sumd_ub <= G.m) st1 = ub;
-    c->st0 = st0;
-    c->st1 = st1;
-    gap_lb = vload(&c->gap_lb);
+    const int64_t gap_raw = dev_gap(sumd_ub, highd_ub, G.two_m, A.alpha, A.beta, G.rtow);
+    if (k == 1) B.st0 = ub;
+    if (B.st1 < 0 && sumd_ub <= G.m) B.st1 = ub;
     sh_i[1] = gap_raw;
-    sh_i[2] = width;
-    sh_i[3] = st0;
-    sh_i[4] = st1;
-    sh_i[5] = gap_lb;
+    sh_i[2] = gap_raw << A.gap_shift;
   }
   __syncthreads();
-  gap_raw = sh_i[1];
-  width = sh_i[2];
-  st0 = sh_i[3];
-  st1 = sh_i[4];
-  gap_lb = sh_i[5];
+  const int64_t gap_raw = sh_i[1], width = sh_i[2];
   const int64_t nlb = ub, nub = ub + width;
-  int64_t nst = (A.flags & EIC_FLAG_NO_PULL)
-                    ? nlb
-                    : block_compute_st(A, P.s3, ub, sumd_ub, gap_lb, gap_raw, nub, st0, st1);
-  // zero the ring slots the next step's statistics will fill: [max(nlb, nub - maxW), nub)
-  {
+  const int64_t nst = (A.flags & EIC_FLAG_NO_PULL)
+                          ? nlb
+                          : block_compute_st(A, P.s3, ub, sumd_ub, B.gap_lb, gap_raw, nub, B.st0, B.st1);
+  {  // zero the ring slots the next statistics pass fills: [max(nlb, nub - maxW), nub)
     const int64_t zl = nub - (int64_t)G.maxw > nlb ? nub - (int64_t)G.maxw : nlb;
     const uint64_t ql = (uint64_t)zl >> A.ring_shift, qu = (uint64_t)(nub - 1) >> A.ring_shift;
     for (uint64_t q = ql + threadIdx.x; q <= qu; q += blockDim.x) __stcg(&A.ring[q & A.ring_mask], 0ull);
@@ -536,58 +649,53 @@ __device__ void step_boundary(const KArgs& A, PhaseScr& P, const Local& L, uint3
     uint32_t scnt = settled_now;
     uint32_t extra = 0;
     if (k == 1 && ub == 0) {  // the source itself was not settled by the first step
-      A.settled[scnt++] = A.s;
+      A.sid[scnt] = A.s;
+      A.sd[scnt] = 0;
+      A.scur[scnt] = kNone;
+      ++scnt;
       extra = 1;
     }
-    // Function 1's push set {lb0 <= dist <= st} from the settled steps
+    // Function 1's push set {lb0 <= dist <= st}: the settled steps j with
+    // ub_j > lb0 (j0, moving forward only) and lb_j <= st (j1, from the back)
     const int64_t lb0 = nlb - (int64_t)G.maxw > 0 ? nlb - (int64_t)G.maxw : 0;
     uint32_t pb = 0, pe = 0;
+    while (B.j0 <= k && __ldcg(&A.step_ub[B.j0]) <= lb0) ++B.j0;
     if (nst >= lb0) {
-      uint32_t lo = 1, hi = k + 1;  // first step j with ub_j > lb0
-      while (lo < hi) {
-        uint32_t mid = (lo + hi) >> 1;
-        if (A.step_ub[mid] > lb0)
-          hi = mid;
-        else
-          lo = mid + 1;
+      uint32_t j1 = k;
+      int64_t lbj = lb;  // lb_k
+      while (j1 >= 1 && lbj > nst) {
+        --j1;
+        lbj = j1 >= 2 ? __ldcg(&A.step_ub[j1 - 1]) : 0;
       }
-      const uint32_t j0 = lo;
-      lo = 1;
-      hi = k;  // last step j with lb_j <= nst (lb_1 = 0, lb_j = ub_{j-1})
-      while (lo < hi) {
-        uint32_t mid = (lo + hi + 1) >> 1;
-        if (A.step_ub[mid - 1] <= nst)
-          lo = mid;
-        else
-          hi = mid - 1;
-      }
-      const uint32_t j1 = lo;
-      if (j0 <= j1) {
-        pb = A.step_off[j0];
-        pe = A.step_off[j1 + 1];
+      if (B.j0 <= j1 && j1 >= 1) {
+        pb = __ldcg(&A.step_off[B.j0]);
+        pe = j1 == k ? settled_now : __ldcg(&A.step_off[j1 + 1]);
       }
     }
-    // Function 1's pull over the unsettled vertices when st < lb
-    uint32_t pull_on = nst < nlb ? 1u : 0u, pull_src = 0, pull_cnt = 0, ul_out = 0;
-    uint32_t ul_valid = vload(&c->ul_valid), ul_sel = vload(&c->ul_sel);
-    if (L.pull_on) {  // the step just finished pulled into ul[L.ul_out]
-      ul_valid = 1;
-      ul_sel = L.ul_out;
-    }
+    // Function 1's pull: unsettled vertices with an edge lighter than ub - st,
+    // a prefix of the weight-ordered non-isolated vertices
+    const uint32_t pull_on = nst < nlb ? 1u : 0u;
+    uint32_t pull_cnt = 0;
     if (pull_on) {
-      if (ul_valid) {
-        pull_src = 1 + ul_sel;
-        pull_cnt = vload(&c->ulcnt[ul_sel]);
-        ul_out = ul_sel ^ 1u;
-      } else {
-        pull_src = 0;
-        pull_cnt = G.nz_count;
-        ul_out = 0;
+      const int64_t bound = nub - nst;  // smallest weight < bound
+      if (bound >= (int64_t)G.nz_lt_len) {
+        if ((uint64_t)bound > G.maxw) {
+          pull_cnt = G.nz_count;
+        } else {
+          uint32_t lo = 0, hi = G.nz_count;
+          while (lo < hi) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if ((int64_t)__ldg(&G.nz[mid].y) < bound)
+              lo = mid + 1;
+            else
+              hi = mid;
+          }
+          pull_cnt = lo;
+        }
+      } else if (bound > 0) {
+        pull_cnt = __ldg(&G.nz_lt[bound]);
       }
-      c->ulcnt[ul_out] = 0;
     }
-    c->ul_valid = ul_valid;
-    c->ul_sel = ul_sel;
     c->settled_cnt = scnt;
     c->lb = nlb;
     c->ub = nub;
@@ -597,14 +705,12 @@ __device__ void step_boundary(const KArgs& A, PhaseScr& P, const Local& L, uint3
     c->push_beg = pb;
     c->push_end = pe;
     c->pull_on = pull_on;
-    c->pull_src = pull_src;
     c->pull_cnt = pull_cnt;
     c->extra_s = extra;
     c->step_off_cur = settled_now;
-    c->ul_out = ul_out;
-    c->sumd_lb = sumd_ub;
-    c->highd_lb = highd_ub;
-    c->gap_lb = gap_raw;
+    B.sumd_lb = sumd_ub;
+    B.highd_lb = highd_ub;
+    B.gap_lb = gap_raw;
     c->acc_deg = 0;
     c->acc_maxd = 0;
     c->acc_any = 0;
@@ -615,36 +721,76 @@ __device__ void step_boundary(const KArgs& A, PhaseScr& P, const Local& L, uint3
   __syncthreads();
 }
 
+// All threads: control values published before the last barrier (one thread
+// loads them from L2, the block shares them).
 __device__ void read_ctl(const Ctl* c, Local& L) {
-  L.lb = vload(&c->lb);
-  L.ub = vload(&c->ub);
-  L.st = vload(&c->st);
-  L.lb0 = vload(&c->lb0);
-  L.step = vload(&c->step);
-  L.push_beg = vload(&c->push_beg);
-  L.push_end = vload(&c->push_end);
-  L.pull_on = vload(&c->pull_on);
-  L.pull_src = vload(&c->pull_src);
-  L.pull_cnt = vload(&c->pull_cnt);
-  L.extra_s = vload(&c->extra_s);
-  L.step_off_cur = vload(&c->step_off_cur);
-  L.ul_out = vload(&c->ul_out);
+  __shared__ Local sL;
+  if (threadIdx.x == 0) {
+    sL.lb = __ldcg(&c->lb);
+    sL.ub = __ldcg(&c->ub);
+    sL.st = __ldcg(&c->st);
+    sL.lb0 = __ldcg(&c->lb0);
+    sL.step = __ldcg(&c->step);
+    sL.push_beg = __ldcg(&c->push_beg);
+    sL.push_end = __ldcg(&c->push_end);
+    sL.pull_on = __ldcg(&c->pull_on);
+    sL.pull_cnt = __ldcg(&c->pull_cnt);
+    sL.extra_s = __ldcg(&c->extra_s);
+    sL.step_off_cur = __ldcg(&c->step_off_cur);
+    sL.done = __ldcg(&c->done);
+  }
+  __syncthreads();
+  const uint32_t rid = L.rid, qsel = L.qsel;
+  L = sL;
+  L.rid = rid;
+  L.qsel = qsel;
+  L.cur_cnt = 0;
+  __syncthreads();
 }
 
-__global__ void __launch_bounds__(1024) k_eic(KArgs A) {
+// Block sum of several counters; thread 0 receives the totals.
+template <int K>
+__device__ __forceinline__ void block_sums(unsigned long long (&v)[K], unsigned long long (*sh)[K]) {
+#pragma unroll
+  for (int j = 0; j < K; ++j) v[j] = warp_sum_u64(v[j]);
+  if ((threadIdx.x & 31) == 0)
+#pragma unroll
+    for (int j = 0; j < K; ++j) sh[threadIdx.x >> 5][j] = v[j];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (uint32_t w = 1; w < (blockDim.x >> 5); ++w)
+#pragma unroll
+      for (int j = 0; j < K; ++j) v[j] += sh[w][j];
+  }
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(kMaxBlock, 2) k_eic(KArgs A) {
   __shared__ PhaseScr P;
-  __shared__ unsigned long long sh_red[32];
+  __shared__ Stage T;
+  __shared__ BState B;
+  __shared__ unsigned long long sh_red[32][6];
+  __shared__ unsigned long long sh_snap[4];
   __shared__ uint32_t sh_last;
   Ctl* c = A.ctl;
-  uint32_t gen = vload(&c->bar.gen);
+  uint32_t gen = __ldcg(&c->bar.gen);
   Local L;
-  read_ctl(c, L);
-  L.rid = vload(&c->round_base);
+  L.rid = __ldcg(&c->round_base);
   L.qsel = 0;
+  read_ctl(c, L);
   L.cur_cnt = 1;  // the first round's frontier is {s}
   Counters C = {0, 0, 0, 0, 0};
-  const uint32_t warp = threadIdx.x >> 5, wpb = blockDim.x >> 5;
-  const uint32_t gwarp = blockIdx.x * wpb + warp, nwarps = gridDim.x * wpb;
+  if (threadIdx.x == 0) {
+    T.qn = T.fn = T.tn = 0;
+    B.st0 = -1;
+    B.st1 = -1;
+    B.gap_lb = __ldcg(&c->gap_lb);
+    B.max_settled = -1;
+    B.sumd_lb = A.G.two_m;
+    B.highd_lb = A.G.highd0;
+    B.j0 = 1;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) tl_mark(A, 0, L.rid);
   bool alive = true;
   uint32_t total_rounds = 0;
   constexpr uint32_t kMaxRounds = 1u << 22;  // every block counts the same rounds and stops together
@@ -662,7 +808,8 @@ __global__ void __launch_bounds__(1024) k_eic(KArgs A) {
       // counters of round rid+1 were last read two barriers ago: clear them now
       if (blockIdx.x == 0 && threadIdx.x == 0) {
         c->qcnt[(L.rid + 1) % 3] = 0;
-        c->heavy_packed[(L.rid + 1) % 3] = 0;
+        c->tcnt[(L.rid + 1) % 3] = 0;
+        c->work[(L.rid + 1) % 3] = 0;
       }
       RoundCtx R;
       R.lb = L.lb;
@@ -674,43 +821,53 @@ __global__ void __launch_bounds__(1024) k_eic(KArgs A) {
       R.step1 = L.step == 1;
       R.qout = L.qsel ? A.q0 : A.q1;
       R.qcnt_out = &c->qcnt[L.rid % 3];
-      R.first_list = R.step1 ? A.touched : A.settled;
+      R.first_list = R.step1 ? A.touched : A.sid;
       R.first_cnt = R.step1 ? &c->touched_cnt : &c->settled_cnt;
-      R.ul_out = L.ul_out ? A.ul1 : A.ul0;
-      R.ulcnt_out = &c->ulcnt[L.ul_out];
-      R.heavy_ctr = &c->heavy_packed[L.rid % 3];
+      R.tcnt = &c->tcnt[L.rid % 3];
+      R.work = &c->work[L.rid % 3];
       const uint32_t* qin = L.qsel ? A.q1 : A.q0;
-      const uint32_t* pull_list = L.pull_src == 0 ? A.G.nz : (L.pull_src == 1 ? A.ul0 : A.ul1);
-      uint32_t nitems;
-      if (round1)
-        nitems = (L.push_end - L.push_beg) + (L.pull_on ? L.pull_cnt : 0) + L.extra_s;
-      else
-        nitems = L.cur_cnt;
-      for (uint32_t base = gwarp * 32; base < nitems; base += nwarps * 32)
-        process_items(A, R, P.w[warp], L, base, nitems, round1, qin, pull_list, C);
+      Local LL = L;
+      if (!L.pull_on) LL.pull_cnt = 0;
+      const uint32_t nitems = round1 ? (LL.push_end - LL.push_beg) + LL.pull_cnt + LL.extra_s : L.cur_cnt;
+      round_phase(A, R, LL, P.r, T, nitems, round1, qin, C);
       if (!grid_barrier(&c->bar, &gen, A.max_spin, &c->status)) {
         alive = false;
         break;
       }
-      const unsigned long long hp = vload(&c->heavy_packed[L.rid % 3]);
+      if (threadIdx.x == 0) {
+        sh_snap[0] = __ldcg(&c->tcnt[L.rid % 3]);
+        sh_snap[1] = __ldcg(&c->qcnt[L.rid % 3]);
+        sh_snap[2] = __ldcg(&c->ub_cand);
+        if (blockIdx.x == 0) tl_mark(A, 1, L.rid);
+      }
+      __syncthreads();
+      const unsigned long long hp = sh_snap[0];
+      L.cur_cnt = (uint32_t)sh_snap[1];
+      uint32_t uc = (uint32_t)sh_snap[2];
+      __syncthreads();
       if (hp != 0) {
-        heavy_phase(A, R, hp, C);
+        task_phase(A, R, (uint32_t)hp, T, C);
         if (!grid_barrier(&c->bar, &gen, A.max_spin, &c->status)) {
           alive = false;
           break;
         }
+        if (blockIdx.x == 0 && threadIdx.x == 0) tl_mark(A, 2, L.rid);
+        if (threadIdx.x == 0) {
+          sh_snap[1] = __ldcg(&c->qcnt[L.rid % 3]);
+          sh_snap[2] = __ldcg(&c->ub_cand);
+        }
+        __syncthreads();
+        L.cur_cnt = (uint32_t)sh_snap[1];
+        uc = (uint32_t)sh_snap[2];
+        __syncthreads();
       }
-      if (R.step1) {
-        const uint32_t uc = vload(&c->ub_cand);
-        if (uc != EIC_INF && (int64_t)uc < L.ub) L.ub = uc;
-      }
-      L.cur_cnt = vload(&c->qcnt[L.rid % 3]);
+      if (R.step1 && uc != EIC_INF && (int64_t)uc < L.ub) L.ub = uc;
       L.qsel ^= 1u;
       ++rin;
       if (L.cur_cnt == 0) break;
     }
     if (!alive) break;
-    // ------------------------------------------------ statistics pass (S2)
+    // ------------------------------------------------ statistics pass
     {
       S2Scr& S = P.s2;
       for (int r = threadIdx.x; r < kShRanks; r += blockDim.x) S.hist[r] = 0;
@@ -720,9 +877,11 @@ __global__ void __launch_bounds__(1024) k_eic(KArgs A) {
         for (int r = threadIdx.x; r < kShRing; r += blockDim.x) S.ring[r] = 0;
       __syncthreads();
       const bool step1 = L.step == 1;
-      const uint32_t* list = step1 ? A.touched : A.settled;
+      const uint32_t* list = step1 ? A.touched : A.sid;
       const uint32_t lbeg = step1 ? 0 : L.step_off_cur;
-      const uint32_t lend = step1 ? vload(&c->touched_cnt) : vload(&c->settled_cnt);
+      if (threadIdx.x == 0) sh_snap[3] = step1 ? __ldcg(&c->touched_cnt) : __ldcg(&c->settled_cnt);
+      __syncthreads();
+      const uint32_t lend = (uint32_t)sh_snap[3];
       unsigned long long bdeg = 0;
       uint32_t bmax = 0, bany = 0;
       const uint32_t nthreads = gridDim.x * blockDim.x;
@@ -740,11 +899,19 @@ __global__ void __launch_bounds__(1024) k_eic(KArgs A) {
           }
         }
         if (step1) {
-          uint32_t slot = warp_append(take, &c->settled_cnt);
-          if (take) __stcg(&A.settled[slot], x);
+          const uint32_t slot = warp_append(take, &c->settled_cnt);
+          if (take) {
+            __stcg(&A.sid[slot], x);
+            __stcg(&A.sd[slot], d);
+            __stcg(&A.scur[slot], kNone);  // the first step's windows used a larger ub
+          }
+        } else if (take) {
+          __stcg(&A.sd[idx], d);
+          __stcg(&A.scur[idx], __ldcg(&A.cursor[x]));
         }
         if (take) {
-          const uint32_t dg = (uint32_t)(__ldg(&A.G.row[x + 1]) - __ldg(&A.G.row[x]));
+          atomicOr(&A.sbits[x >> 5], 1u << (x & 31));
+          const uint32_t dg = __ldg(&A.G.row[x + 1]) - __ldg(&A.G.row[x]);
           if (dg > 0) {  // degree-0 vertices (an isolated source) carry no rank
             const uint32_t r = __ldg(&A.G.drank[dg]);
             if (r < (uint32_t)kShRanks)
@@ -769,7 +936,6 @@ __global__ void __launch_bounds__(1024) k_eic(KArgs A) {
       if (ring_sh)
         for (int r = threadIdx.x; r < kShRing && r < L.ub - wlo; r += blockDim.x)
           if (S.ring[r]) atomicAdd(&A.ring[((uint64_t)(wlo + r)) & A.ring_mask], S.ring[r]);
-      const unsigned long long tdeg = block_sum_u64(bdeg, sh_red);
       for (int o = 16; o > 0; o >>= 1) {
         bmax = max(bmax, __shfl_xor_sync(EIC_FULL_MASK, bmax, o));
         bany |= __shfl_xor_sync(EIC_FULL_MASK, bany, o);
@@ -778,37 +944,46 @@ __global__ void __launch_bounds__(1024) k_eic(KArgs A) {
         atomicMax(&c->acc_maxd, bmax);
         atomicOr(&c->acc_any, 1u);
       }
-      const unsigned long long f = block_sum_u64(C.frontier, sh_red);
-      const unsigned long long tr = block_sum_u64(C.trav, sh_red);
-      const unsigned long long pl = block_sum_u64(C.pulls, sh_red);
-      const unsigned long long im = block_sum_u64(C.improved, sh_red);
-      const unsigned long long hv = block_sum_u64(C.heavy, sh_red);
+      unsigned long long v[6] = {bdeg, C.frontier, C.trav, C.pulls, C.improved, C.heavy};
+      block_sums<6>(v, sh_red);
       C = {0, 0, 0, 0, 0};
       if (threadIdx.x == 0) {
-        if (tdeg) atomicAdd(&c->acc_deg, tdeg);
-        atomicAdd(&c->cnt_frontier, f);
-        atomicAdd(&c->cnt_trav, tr);
-        atomicAdd(&c->cnt_pulls, pl);
-        atomicAdd(&c->cnt_improved, im);
-        atomicAdd(&c->cnt_heavy, hv);
+        if (v[0]) atomicAdd(&c->acc_deg, v[0]);
+        atomicAdd(&c->cnt_frontier, v[1]);
+        atomicAdd(&c->cnt_trav, v[2]);
+        atomicAdd(&c->cnt_pulls, v[3]);
+        atomicAdd(&c->cnt_improved, v[4]);
+        atomicAdd(&c->cnt_heavy, v[5]);
         __threadfence();
-        sh_last = atomicAdd(&c->s2_done, 1u) == gridDim.x - 1 ? 1u : 0u;
+        atomicAdd(&c->s2_done, 1u);
       }
-      __syncthreads();
-      if (sh_last) {
-        __threadfence();
-        if (threadIdx.x == 0) c->cnt_rounds += rin;
-        step_boundary(A, P, L, rin);
+      if (blockIdx.x == 0) {  // block 0 waits (bounded) for every block's statistics
+        if (threadIdx.x == 0) {
+          uint64_t spins = 0;
+          sh_last = 1;
+          while (ld_acquire_u32(&c->s2_done) < gridDim.x) {
+            if (ld_volatile_int(&c->status) != 0 || ++spins > A.max_spin) {
+              atomicCAS(&c->status, 0, EIC_ETIMEOUT);
+              sh_last = 0;
+              break;
+            }
+          }
+          __threadfence();
+          tl_mark(A, 4, L.rid);
+        }
+        __syncthreads();
+        if (sh_last) step_boundary(A, P, B, L, rin);
+        if (threadIdx.x == 0) tl_mark(A, 5, L.rid);
       }
     }
     if (!grid_barrier(&c->bar, &gen, A.max_spin, &c->status)) break;
-    if (vload(&c->done)) break;
+    if (blockIdx.x == 0 && threadIdx.x == 0) tl_mark(A, 3, L.rid);
     read_ctl(c, L);
-    L.cur_cnt = 0;
+    if (L.done) break;
   }
   // the next query's stamp ids start above every id any block used
   if (threadIdx.x == 0) atomicMax(&c->round_base, L.rid);
-  if (blockIdx.x == 0 && threadIdx.x == 0 && A.status_out) *A.status_out = vload(&c->status);
+  if (blockIdx.x == 0 && threadIdx.x == 0 && A.status_out) *A.status_out = ld_volatile_int(&c->status);
 }
 
 __global__ void k_init(KArgs A) {
@@ -822,7 +997,7 @@ __global__ void k_init(KArgs A) {
     A.touched[0] = A.s;
     A.step_off[1] = 0;
     A.step_ub[0] = 0;
-    const uint64_t dgs = G.row[A.s + 1] - G.row[A.s];
+    const uint32_t dgs = G.row[A.s + 1] - G.row[A.s];
     c->lb = 0;
     c->ub = EIC_INF_T;
     c->st = 0;
@@ -830,25 +1005,23 @@ __global__ void k_init(KArgs A) {
     c->step = 1;
     c->done = 0;
     c->push_beg = c->push_end = 0;
-    c->pull_on = c->pull_src = c->pull_cnt = c->extra_s = 0;
+    c->pull_on = c->pull_cnt = c->extra_s = 0;
     c->step_off_cur = 0;
-    c->ul_out = 0;
     c->st0 = -1;
     c->st1 = -1;
     c->sumd_lb = G.two_m;
     c->highd_lb = G.highd0;
     c->gap_lb = dev_gap(G.two_m, G.highd0, G.two_m, A.alpha, A.beta, G.rtow);
     c->max_settled = -1;
-    c->ul_sel = 0;
-    c->ul_valid = 0;
     c->rounds_in_step = 0;
     c->trace_len = 0;
+    c->tl_len = 0;
     c->qcnt[0] = c->qcnt[1] = c->qcnt[2] = 0;
+    c->work[0] = c->work[1] = c->work[2] = 0;
     c->settled_cnt = 0;
     c->touched_cnt = 1;
-    c->ulcnt[0] = c->ulcnt[1] = 0;
     c->ub_cand = (G.highd0 > 0 && dgs >= G.highd0) ? 0u : EIC_INF;
-    c->heavy_packed[0] = c->heavy_packed[1] = c->heavy_packed[2] = 0;
+    c->tcnt[0] = c->tcnt[1] = c->tcnt[2] = 0;
     c->s2_done = 0;
     c->acc_maxd = 0;
     c->acc_deg = 0;
@@ -867,8 +1040,8 @@ __global__ void k_parent(DevGraph G, const uint32_t* __restrict__ dist, uint32_t
     const uint32_t dv = dist[v];
     uint32_t best = EIC_INF;
     if (v != s && dv != EIC_INF) {
-      const uint64_t rb = G.row[v], re = G.row[v + 1];
-      for (uint64_t i = rb + lane; i < re; i += 32) {
+      const uint32_t rb = G.row[v], re = G.row[v + 1];
+      for (uint32_t i = rb + lane; i < re; i += 32) {
         const uint2 ent = G.adj[i];
         if (ent.y > dv) break;
         const uint32_t du = dist[ent.x];
@@ -888,8 +1061,10 @@ namespace {
 
 constexpr uint32_t kStepCap = 1u << 20;     // steps per query
 constexpr uint32_t kTraceCap = 1u << 16;    // trace rows kept on the device
-constexpr uint32_t kHeavyMinFloor = 256;    // smallest accepted heavy_min
-constexpr uint32_t kDefaultHeavyMin = 2048;
+constexpr uint32_t kTimelineCap = 1u << 16; // diagnostic timeline events
+constexpr uint32_t kHeavyMinFloor = 16;     // smallest accepted heavy_min (bounds the task list)
+constexpr uint32_t kHeavyMinCeil = 4096;
+constexpr uint32_t kDefaultHeavyMin = 32;
 constexpr int kDefaultBlock = 512;
 constexpr uint32_t kDefaultSpinLog2 = 22;
 
@@ -915,10 +1090,10 @@ int resolve_params(const eic_params* in, eic_params* out) {
   if (out->st_num == 0) return EIC_EINVAL;
   if (out->gap_shift > 16) return EIC_EINVAL;
   if (out->block_threads != 0 &&
-      (out->block_threads % 32 != 0 || out->block_threads < 128 || out->block_threads > 1024))
+      (out->block_threads % 32 != 0 || out->block_threads < 128 || out->block_threads > kMaxBlock))
     return EIC_EINVAL;
   if (out->heavy_min == 0) out->heavy_min = kDefaultHeavyMin;
-  if (out->heavy_min < kHeavyMinFloor) return EIC_EINVAL;
+  if (out->heavy_min < kHeavyMinFloor || out->heavy_min > kHeavyMinCeil) return EIC_EINVAL;
   if (out->max_spin_log2 == 0) out->max_spin_log2 = kDefaultSpinLog2;
   if (out->max_spin_log2 > 40) return EIC_EINVAL;
   return EIC_OK;
@@ -954,15 +1129,17 @@ KArgs make_args(eic_graph* g, uint32_t s, uint32_t* dist, const eic_params& p, i
   A.G = g->dg;
   A.dist = dist;
   A.stamp = w.stamp;
+  A.cursor = w.cursor;
   A.q0 = w.q[0];
   A.q1 = w.q[1];
-  A.settled = w.settled;
+  A.sid = w.sid;
+  A.sd = w.sd;
+  A.scur = w.scur;
   A.touched = w.touched;
-  A.ul0 = w.ul[0];
-  A.ul1 = w.ul[1];
+  A.sbits = w.sbits;
   A.hist = w.hist;
   A.ring = w.ring;
-  A.heavy = w.heavy;
+  A.tasks = w.tasks;
   A.step_ub = w.step_ub;
   A.step_off = w.step_off;
   A.trace = w.trace;
@@ -978,15 +1155,17 @@ KArgs make_args(eic_graph* g, uint32_t s, uint32_t* dist, const eic_params& p, i
   A.flags = p.flags;
   A.ring_mask = (1u << w.ring_bits) - 1u;
   A.ring_shift = w.ring_shift;
-  A.heavy_cap = w.heavy_cap;
+  A.task_cap = w.task_cap;
   A.step_cap = w.step_cap;
   A.trace_cap = kTraceCap;
+  A.timeline = nullptr;
+  A.timeline_cap = 0;
   return A;
 }
 
 // Enqueue one query: dist <- +inf, init, persistent kernel, optional parent.
 int enqueue_query(eic_graph* g, uint32_t s, uint32_t* dist, uint32_t* parent, const eic_params& p, int* status_out,
-                  cudaStream_t st) {
+                  cudaStream_t st, bool timeline = false) {
   Workspace& w = g->ws;
   const int block = p.block_threads ? (int)p.block_threads : kDefaultBlock;
   int rc = launch_shape(&w, block);
@@ -997,7 +1176,12 @@ int enqueue_query(eic_graph* g, uint32_t s, uint32_t* dist, uint32_t* parent, co
     w.host_round_base = 0;
   }
   EIC_CUDA_TRY(cudaMemsetAsync(dist, 0xFF, (uint64_t)g->dg.n * 4, st));
+  EIC_CUDA_TRY(cudaMemsetAsync(w.sbits, 0, ((uint64_t)g->dg.n / 32 + 2) * 4, st));
   KArgs A = make_args(g, s, dist, p, status_out);
+  if (timeline) {
+    A.timeline = w.timeline;
+    A.timeline_cap = kTimelineCap;
+  }
   k_init<<<64, 256, 0, st>>>(A);
   EIC_CUDA_TRY(cudaGetLastError());
   void* args[] = {&A};
@@ -1027,16 +1211,19 @@ void eic_ws_free(Workspace* w) {
   cudaFree(w->stamp);
   cudaFree(w->q[0]);
   cudaFree(w->q[1]);
-  cudaFree(w->settled);
+  cudaFree(w->sid);
+  cudaFree(w->sd);
+  cudaFree(w->scur);
+  cudaFree(w->cursor);
   cudaFree(w->touched);
-  cudaFree(w->ul[0]);
-  cudaFree(w->ul[1]);
+  cudaFree(w->sbits);
   cudaFree(w->hist);
   cudaFree(w->ring);
-  cudaFree(w->heavy);
+  cudaFree(w->tasks);
   cudaFree(w->step_ub);
   cudaFree(w->step_off);
   cudaFree(w->trace);
+  cudaFree(w->timeline);
   cudaFree(w->ctl);
   if (w->ctl_host) cudaFreeHost(w->ctl_host);
   *w = Workspace();
@@ -1053,15 +1240,17 @@ int eic_ws_ensure(eic_graph* g, int) {
   while (bits < 32 && (1ull << bits) <= maxw) ++bits;  // 2^bits > maxW
   w->ring_bits = bits < 20 ? bits : 20;
   w->ring_shift = bits > 20 ? bits - 20 : 0;
-  w->heavy_cap = (uint32_t)(G.two_m / kHeavyMinFloor + 2);
+  // a window longer than heavy_min >= 16 yields ceil(len / 64) <= len / 16 tasks,
+  // and the windows of one round belong to distinct vertices
+  w->task_cap = (uint32_t)(G.two_m / kHeavyMinFloor + 2);
   w->step_cap = kStepCap;
   w->n = G.n;
   if ((rc = walloc(w, &w->stamp, n)) || (rc = walloc(w, &w->q[0], n)) || (rc = walloc(w, &w->q[1], n)) ||
-      (rc = walloc(w, &w->settled, n + 2)) || (rc = walloc(w, &w->touched, n + 1)) ||
-      (rc = walloc(w, &w->ul[0], (uint64_t)G.nz_count + 1)) || (rc = walloc(w, &w->ul[1], (uint64_t)G.nz_count + 1)) ||
+      (rc = walloc(w, &w->sid, n + 2)) || (rc = walloc(w, &w->sd, n + 2)) ||
+      (rc = walloc(w, &w->scur, n + 2)) || (rc = walloc(w, &w->cursor, n)) || (rc = walloc(w, &w->touched, n + 1)) || (rc = walloc(w, &w->sbits, n / 32 + 2)) ||
       (rc = walloc(w, &w->hist, (uint64_t)G.D + 1)) || (rc = walloc(w, &w->ring, 1ull << w->ring_bits)) ||
-      (rc = walloc(w, &w->heavy, w->heavy_cap)) || (rc = walloc(w, &w->step_ub, (uint64_t)kStepCap + 2)) ||
-      (rc = walloc(w, &w->step_off, (uint64_t)kStepCap + 2)) || (rc = walloc(w, &w->trace, kTraceCap)) ||
+      (rc = walloc(w, &w->tasks, w->task_cap)) || (rc = walloc(w, &w->step_ub, (uint64_t)kStepCap + 2)) ||
+      (rc = walloc(w, &w->step_off, (uint64_t)kStepCap + 2)) || (rc = walloc(w, &w->trace, kTraceCap)) || (rc = walloc(w, &w->timeline, 2ull * kTimelineCap)) ||
       (rc = walloc(w, &w->ctl, 1))) {
     eic_ws_free(w);
     return rc;
@@ -1095,14 +1284,18 @@ int eic_sssp(const eic_graph* gc, uint32_t source, uint32_t* dist, uint32_t* par
   cudaStream_t st = (cudaStream_t)stream;
   eic_step* trace = stats ? stats->trace : nullptr;
   const uint64_t trace_cap = stats ? stats->trace_cap : 0;
+  uint64_t* tl = stats ? stats->timeline : nullptr;
+  const uint64_t tl_cap = stats ? stats->timeline_cap : 0;
   if (stats) {
     memset(stats, 0, sizeof(*stats));
     stats->trace = trace;
     stats->trace_cap = trace_cap;
+    stats->timeline = tl;
+    stats->timeline_cap = tl_cap;
   }
   if (g->dg.two_m == 0) return trivial_query(g, source, dist, parent, st);
   if ((rc = eic_ws_ensure(g, 0))) return rc;
-  if ((rc = enqueue_query(g, source, dist, parent, p, nullptr, st))) {
+  if ((rc = enqueue_query(g, source, dist, parent, p, nullptr, st, tl && tl_cap))) {
     cudaStreamSynchronize(st);
     (void)cudaGetLastError();
     return rc;
@@ -1125,6 +1318,12 @@ int eic_sssp(const eic_graph* gc, uint32_t source, uint32_t* dist, uint32_t* par
       uint64_t rows = h.trace_len < trace_cap ? h.trace_len : trace_cap;
       if (rows > kTraceCap) rows = kTraceCap;
       if (rows) EIC_CUDA_TRY(cudaMemcpy(trace, w.trace, rows * sizeof(eic_step), cudaMemcpyDeviceToHost));
+    }
+    if (tl && tl_cap) {
+      uint64_t ev = h.tl_len < tl_cap ? h.tl_len : tl_cap;
+      if (ev > kTimelineCap) ev = kTimelineCap;
+      stats->timeline_len = h.tl_len;
+      if (ev) EIC_CUDA_TRY(cudaMemcpy(tl, w.timeline, ev * 16, cudaMemcpyDeviceToHost));
     }
   }
   return h.status;

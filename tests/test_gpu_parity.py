@@ -104,7 +104,7 @@ def test_no_pull_and_step_scaling_stay_exact():
     for s in wl.sources:
         want, _ = og.dijkstra(int(s))
         for p in (eic.default_params(flags=eic.FLAG_NO_PULL), eic.default_params(gap_shift=2),
-                  eic.default_params(heavy_min=256), eic.default_params(block_threads=256),
+                  eic.default_params(heavy_min=16), eic.default_params(heavy_min=4096), eic.default_params(block_threads=256), eic.default_params(block_threads=128),
                   eic.default_params(st_num=7)):
             dist, rc, _ = eic.sssp(g, int(s), params=p)
             assert np.array_equal(eic.to_host_u32(dist), want)
