@@ -1,0 +1,347 @@
+#!/usr/bin/env python3
+"""GTEPS of single-source EIC queries on one GB300 (and N independent replicas).
+
+Workload (default): RMAT/Kronecker scale 25, edge factor 16, a,b,c,d =
+0.57,0.19,0.19,0.05, vertex ids permuted, integer weights uniform in [1, 255],
+symmetrised and deduplicated on the device; 64 sources drawn uniformly from
+the non-isolated vertices. A step is one pass of the whole query path
+(Algorithm 1 with Function 1/2, exact distances) for the 64 sources on the
+resident graph. The graph build (preprocessing, Section 4.1) is timed
+separately and reported as build_s.
+
+  value    = sum over queries of m_c (undirected edges in the source's
+             component, Graph500 convention) / device time of the step, summed
+             over ranks (replicas) with the max step time over ranks.
+  e2e      = the same metric with every step's sources copied from pinned host
+             memory and every query's distance array copied back to pinned host
+             memory inside the timed region.
+  roofline = algorithmic bytes of the query kernel per launch (frontier items
+             16 B, traversed entries 12 B, successful relaxations 8 B, pulled
+             vertices 12 B, plus 4n for dist) over the CUDA-event duration of
+             one query, against the measured HBM copy bandwidth.
+
+--impl reference runs the CPU oracle (binary-heap Dijkstra) on the host cores
+for a bounded sample of the same workload and prints the same JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "GTEPS single-source & batched vs plain path on 1 GB300; p50/p99 query latency"
+
+
+def parse_args():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--scale", type=int, default=25, help="Kronecker scale of the workload")
+    ap.add_argument("--sources", type=int, default=64)
+    ap.add_argument("--cpu-sample", type=int, default=1, help="oracle queries timed for cpu_baseline")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", str(rank)))
+    return rank, world, local
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        if self.proc is None:
+            return out
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return out
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[j] for r in rows for j in range(4) if r[5 + j].lower() == "active"})
+        out.update(sm_mhz=statistics.median(sm) if sm else None, sm_max_mhz=max(mx) if mx else None,
+                   reasons=reasons, samples=len(rows))
+        return out
+
+
+def make_workload(scale: int, nsources: int):
+    from paper_2506_19349_gb300 import graphgen
+
+    return graphgen.kron(scale, seed=2, nsources=nsources)
+
+
+def workload_config(wl, scale, nsources):
+    return {"workload": f"kron{scale}: RMAT(0.57,0.19,0.19,0.05) scale {scale} edgefactor 16, ids permuted, "
+                        f"weights uniform [1,255], {nsources} sources uniform over non-isolated vertices",
+            "n": int(wl.n), "tuples": int(wl.num_tuples), "queries_per_step": nsources,
+            "l2": "inputs larger than L2 (CSR of the resident graph)", "path": "plain single-source, one "
+                                                                          "persistent launch per query"}
+
+
+def oracle_baseline(wl, sample: int, m_c_of):
+    """Time the oracle's Dijkstra (one host thread) on `sample` sources."""
+    import oracle
+
+    og = oracle.Graph(wl.n, wl.src, wl.dst, wl.w)
+    total_edges, total_t = 0, 0.0
+    for s in wl.sources[:sample]:
+        t0 = time.perf_counter()
+        d, rc = og.dijkstra(int(s))
+        total_t += time.perf_counter() - t0
+        total_edges += m_c_of(og, d)
+    return og, total_edges / total_t / 1e9, total_t
+
+
+def oracle_m_c(og, d):
+    import numpy as np
+
+    deg = og.degrees()
+    return int(deg[d != 0xFFFFFFFF].sum() // 2)
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    wl = make_workload(args.scale, args.sources)
+    import oracle
+
+    og = oracle.Graph(wl.n, wl.src, wl.dst, wl.w)
+    srcs = [int(s) for s in wl.sources]
+    times, edges = [], []
+    for k in range(args.warmup + args.steps):
+        s = srcs[k % len(srcs)]
+        t0 = time.perf_counter()
+        d, rc = og.dijkstra(s)
+        dt = time.perf_counter() - t0
+        if k >= args.warmup:
+            times.append(dt)
+            edges.append(oracle_m_c(og, d))
+    value = sum(edges) / sum(times) / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "GTEPS", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+            "data": "synthetic", "config": workload_config(wl, args.scale, args.sources),
+            "cpu_baseline": {"value": value, "unit": "GTEPS", "cores": 1, "kind": "oracle",
+                             "sample": f"one binary-heap Dijkstra query per step on kron{args.scale} (CPU "
+                                       f"oracle), sources cycling through the workload's list"},
+            "e2e": {"value": value, "unit": "GTEPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import numpy as np
+    import torch
+
+    rank, world, local = dist_env()
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA device")
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    from paper_2506_19349_gb300 import build as libbuild
+
+    if not os.path.exists(os.path.join(ROOT, "paper_2506_19349_gb300", "libeic.so")):
+        libbuild.build()
+    import paper_2506_19349_gb300 as eic
+
+    t0 = time.perf_counter()
+    wl = make_workload(args.scale, args.sources)
+    gen_s = time.perf_counter() - t0
+    stream = torch.cuda.current_stream()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    g = eic.Graph(wl.n, wl.src, wl.dst, wl.w)
+    torch.cuda.synchronize()
+    build_s = time.perf_counter() - t0
+    n = g.n
+    srcs = [int(s) for s in wl.sources]
+    q = len(srcs)
+    dists = [eic.new_dist(n) for _ in range(q)]
+    # degrees for m_c (edges in the source's component)
+    rowp = np.empty(n + 1, dtype=np.uint64)
+    import ctypes
+
+    eic.load_library().eic_graph_export(g.handle, rowp.ctypes.data, None, None, None)
+    deg = torch.from_numpy(np.diff(rowp).astype(np.int64)).cuda()
+    del rowp
+
+    def run_step(collect=False):
+        evs = []
+        infos = []
+        for i, s in enumerate(srcs):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            _, rc, info = eic.sssp(g, s, dist=dists[i], stats=collect)
+            e1.record(stream)
+            evs.append((e0, e1))
+            infos.append(info)
+        return evs, infos
+
+    # warm-up (also yields m_c per source)
+    for _ in range(max(args.warmup, 1)):
+        run_step()
+    torch.cuda.synchronize()
+    m_c = [int(deg[d != -1].sum().item() // 2) for d in dists]
+    edges_per_step = sum(m_c)
+
+    # ---- timed region: device time with inputs resident
+    sampler = ClockSampler(local)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    start = torch.cuda.Event(enable_timing=True)
+    end = torch.cuda.Event(enable_timing=True)
+    start.record(stream)
+    per_query = []
+    all_infos = []
+    for _ in range(args.steps):
+        evs, infos = run_step(collect=True)
+        per_query.append(evs)
+        all_infos.extend(infos)
+    end.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = sampler.stop()
+    total_ms = start.elapsed_time(end)
+    q_ms = [a.elapsed_time(b) for evs in per_query for a, b in evs]
+    if world > 1:
+        t = torch.tensor([total_ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = world * edges_per_step * args.steps / (total_ms * 1e-3) / 1e9
+
+    # roofline of the query kernel: algorithmic bytes per launch over its event duration
+    b_alg = [16 * inf["frontier"] + 12 * inf["traversed"] + 8 * inf["improved"] + 12 * inf["pull_items"] + 4 * n
+             for inf in all_infos]
+    achieved = statistics.mean(b / (t * 1e-3) / 1e9 for b, t in zip(b_alg, q_ms))
+    peak, peak_kind = peaks()
+
+    # ---- end to end: sources from pinned host memory, distances back to pinned host memory
+    e2e = None
+    if not args.no_e2e:
+        src_host = torch.tensor(srcs, dtype=torch.int32).pin_memory()
+        src_dev = torch.empty(q, dtype=torch.int32, device="cuda")
+        host_out = [torch.empty(n, dtype=torch.int32).pin_memory() for _ in range(2)]
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        e_start = torch.cuda.Event(enable_timing=True)
+        e_end = torch.cuda.Event(enable_timing=True)
+        e_start.record(stream)
+        for _ in range(args.steps):
+            src_dev.copy_(src_host, non_blocking=True)
+            srcs_now = src_dev.cpu().tolist()  # the query API takes host source ids
+            for i, s in enumerate(srcs_now):
+                eic.sssp(g, s, dist=dists[i])
+                host_out[i & 1].copy_(dists[i], non_blocking=True)
+        e_end.record(stream)
+        torch.cuda.synchronize()
+        e2e_ms = e_start.elapsed_time(e_end)
+        if world > 1:
+            t = torch.tensor([e2e_ms], device="cuda")
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            e2e_ms = float(t.item())
+        e2e = {"value": world * edges_per_step * args.steps / (e2e_ms * 1e-3) / 1e9, "unit": "GTEPS",
+               "h2d_bytes_per_step": 4 * q, "d2h_bytes_per_step": 4 * n * q}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        _, cpu_gteps, cpu_t = oracle_baseline(wl, args.cpu_sample, oracle_m_c)
+        cpu = {"value": cpu_gteps, "unit": "GTEPS", "cores": 1, "kind": "oracle",
+               "sample": f"{args.cpu_sample} binary-heap Dijkstra quer{'y' if args.cpu_sample == 1 else 'ies'} "
+                         f"of the same kron{args.scale} workload on one host thread ({cpu_t:.1f} s; oracle CSR "
+                         f"build untimed); host has {os.cpu_count()} cores"}
+
+    if rank == 0:
+        q_sorted = sorted(q_ms)
+        line = {
+            "metric": METRIC, "value": value, "unit": "GTEPS", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": workload_config(wl, args.scale, q) | {"m": int(g.m), "m_c_mean": statistics.mean(m_c),
+                                                            "build_s": build_s, "generate_s": gen_s},
+            "latency_ms": {"p50": q_sorted[len(q_sorted) // 2], "p99": q_sorted[min(len(q_sorted) - 1,
+                                                                                      int(0.99 * len(q_sorted)))],
+                           "mean": statistics.mean(q_ms)},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
+                         "kernel": "k_eic (one launch per query, duration includes its dist/bitmap memsets)"},
+            "cpu_baseline": cpu, "clocks": clocks, "e2e": e2e, "gpu_launches": 2 * q * args.steps,
+            "counters_mean": {k: statistics.mean(inf[k] for inf in all_infos)
+                              for k in ("steps", "rounds", "frontier", "traversed", "pulls", "improved", "heavy",
+                                        "pull_items")},
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

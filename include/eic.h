@@ -91,6 +91,7 @@ typedef struct {
   uint64_t pulls;      /* pull requests (entries examined by Function 1's pull) */
   uint64_t improved;   /* successful relaxations */
   uint64_t heavy;      /* 64-entry tasks spread over the grid */
+  uint64_t pull_items; /* unsettled vertices whose light prefix a pull read */
   eic_step* trace;
   uint64_t trace_cap;
   uint64_t trace_len;

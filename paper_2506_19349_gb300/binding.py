@@ -41,7 +41,8 @@ class Step(ctypes.Structure):
 class Stats(ctypes.Structure):
     _fields_ = [("steps", ctypes.c_uint64), ("rounds", ctypes.c_uint64), ("frontier", ctypes.c_uint64),
                 ("traversed", ctypes.c_uint64), ("pulls", ctypes.c_uint64), ("improved", ctypes.c_uint64),
-                ("heavy", ctypes.c_uint64), ("trace", ctypes.POINTER(Step)), ("trace_cap", ctypes.c_uint64),
+                ("heavy", ctypes.c_uint64), ("pull_items", ctypes.c_uint64), ("trace", ctypes.POINTER(Step)),
+                ("trace_cap", ctypes.c_uint64),
                 ("trace_len", ctypes.c_uint64), ("timeline", ctypes.POINTER(ctypes.c_uint64)),
                 ("timeline_cap", ctypes.c_uint64), ("timeline_len", ctypes.c_uint64)]
 

@@ -41,7 +41,7 @@ struct Ctl {
   unsigned long long acc_deg;
   uint32_t acc_any;
   uint32_t round_base;  // stamp id of the last round of the previous query
-  unsigned long long cnt_rounds, cnt_frontier, cnt_trav, cnt_pulls, cnt_improved, cnt_heavy;
+  unsigned long long cnt_rounds, cnt_frontier, cnt_trav, cnt_pulls, cnt_improved, cnt_heavy, cnt_pitems;
   GridBarrier bar;
   int status;
 };

@@ -137,7 +137,7 @@ struct BState {
 };
 
 struct Counters {
-  unsigned long long frontier, trav, pulls, improved, heavy;
+  unsigned long long frontier, trav, pulls, improved, heavy, pitems;
 };
 
 __device__ __forceinline__ void tl_mark(const KArgs& A, uint32_t kind, uint32_t rid) {
@@ -360,6 +360,7 @@ __device__ void round_phase(const KArgs& A, const RoundCtx& R, const Local& L, R
         mode = kModePull;
         const uint32_t bits = __ldcg(&A.sbits[u >> 5]);
         if (!((bits >> (u & 31)) & 1u)) {
+          C.pitems += 1;
           // the row's first weight is below the bound (nz order): gallop from the second
           b = __ldg(&A.G.row[u]);
           len = gallop_w(A.G.adj, b + 1, __ldg(&A.G.row[u + 1]), pull_bound) - b;
@@ -769,7 +770,7 @@ __global__ void __launch_bounds__(kMaxBlock, 2) k_eic(KArgs A) {
   __shared__ PhaseScr P;
   __shared__ Stage T;
   __shared__ BState B;
-  __shared__ unsigned long long sh_red[32][6];
+  __shared__ unsigned long long sh_red[32][7];
   __shared__ unsigned long long sh_snap[4];
   __shared__ uint32_t sh_last;
   Ctl* c = A.ctl;
@@ -779,7 +780,7 @@ __global__ void __launch_bounds__(kMaxBlock, 2) k_eic(KArgs A) {
   L.qsel = 0;
   read_ctl(c, L);
   L.cur_cnt = 1;  // the first round's frontier is {s}
-  Counters C = {0, 0, 0, 0, 0};
+  Counters C = {0, 0, 0, 0, 0, 0};
   if (threadIdx.x == 0) {
     T.qn = T.fn = T.tn = 0;
     B.st0 = -1;
@@ -944,9 +945,9 @@ __global__ void __launch_bounds__(kMaxBlock, 2) k_eic(KArgs A) {
         atomicMax(&c->acc_maxd, bmax);
         atomicOr(&c->acc_any, 1u);
       }
-      unsigned long long v[6] = {bdeg, C.frontier, C.trav, C.pulls, C.improved, C.heavy};
-      block_sums<6>(v, sh_red);
-      C = {0, 0, 0, 0, 0};
+      unsigned long long v[7] = {bdeg, C.frontier, C.trav, C.pulls, C.improved, C.heavy, C.pitems};
+      block_sums<7>(v, sh_red);
+      C = {0, 0, 0, 0, 0, 0};
       if (threadIdx.x == 0) {
         if (v[0]) atomicAdd(&c->acc_deg, v[0]);
         atomicAdd(&c->cnt_frontier, v[1]);
@@ -954,6 +955,7 @@ __global__ void __launch_bounds__(kMaxBlock, 2) k_eic(KArgs A) {
         atomicAdd(&c->cnt_pulls, v[3]);
         atomicAdd(&c->cnt_improved, v[4]);
         atomicAdd(&c->cnt_heavy, v[5]);
+        atomicAdd(&c->cnt_pitems, v[6]);
         __threadfence();
         atomicAdd(&c->s2_done, 1u);
       }
@@ -1027,6 +1029,7 @@ __global__ void k_init(KArgs A) {
     c->acc_deg = 0;
     c->acc_any = 0;
     c->cnt_rounds = c->cnt_frontier = c->cnt_trav = c->cnt_pulls = c->cnt_improved = c->cnt_heavy = 0;
+    c->cnt_pitems = 0;
     c->bar.count = 0;
     c->status = 0;
   }
@@ -1268,6 +1271,17 @@ int eic_ws_ensure(eic_graph* g, int) {
   return EIC_OK;
 }
 
+namespace {
+constexpr int kMaxDevices = 64;
+struct BatchBuffers {  // per-device status arrays of eic_sssp_batch, kept for reuse
+  int* dstat = nullptr;
+  int* hstat = nullptr;
+  uint32_t cap = 0;
+};
+BatchBuffers g_batch[kMaxDevices];
+std::mutex g_batch_mu;
+}  // namespace
+
 extern "C" {
 
 int eic_sssp(const eic_graph* gc, uint32_t source, uint32_t* dist, uint32_t* parent, const eic_params* params,
@@ -1313,6 +1327,7 @@ int eic_sssp(const eic_graph* gc, uint32_t source, uint32_t* dist, uint32_t* par
     stats->pulls = h.cnt_pulls;
     stats->improved = h.cnt_improved;
     stats->heavy = h.cnt_heavy;
+    stats->pull_items = h.cnt_pitems;
     stats->trace_len = h.trace_len;
     if (trace && trace_cap) {
       uint64_t rows = h.trace_len < trace_cap ? h.trace_len : trace_cap;
@@ -1344,14 +1359,28 @@ int eic_sssp_batch(const eic_graph* const* graphs, const uint32_t* sources, uint
     }
   }
   cudaStream_t st = (cudaStream_t)stream;
-  int* dstat = nullptr;
-  int* hstat = nullptr;
-  if (cudaMalloc((void**)&dstat, num_queries * sizeof(int)) != cudaSuccess ||
-      cudaMallocHost((void**)&hstat, num_queries * sizeof(int)) != cudaSuccess) {
+  std::lock_guard<std::mutex> block(g_batch_mu);
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
     (void)cudaGetLastError();
-    cudaFree(dstat);
-    return EIC_ENOMEM;
+    return EIC_ECUDA;
   }
+  BatchBuffers& bb = g_batch[dev];
+  if (bb.cap < num_queries) {
+    cudaFree(bb.dstat);
+    if (bb.hstat) cudaFreeHost(bb.hstat);
+    bb.dstat = nullptr;
+    bb.hstat = nullptr;
+    bb.cap = 0;
+    if (cudaMalloc((void**)&bb.dstat, num_queries * sizeof(int)) != cudaSuccess ||
+        cudaMallocHost((void**)&bb.hstat, num_queries * sizeof(int)) != cudaSuccess) {
+      (void)cudaGetLastError();
+      return EIC_ENOMEM;
+    }
+    bb.cap = num_queries;
+  }
+  int* dstat = bb.dstat;
+  int* hstat = bb.hstat;
   cudaMemsetAsync(dstat, 0, num_queries * sizeof(int), st);
   int first_err = EIC_OK;
   for (uint32_t i = 0; i < num_queries && first_err == EIC_OK; ++i) {
@@ -1383,8 +1412,6 @@ int eic_sssp_batch(const eic_graph* const* graphs, const uint32_t* sources, uint
         (void)cudaGetLastError();
     }
   }
-  cudaFree(dstat);
-  cudaFreeHost(hstat);
   return first_err;
 }
 
