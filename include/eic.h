@@ -34,6 +34,7 @@ extern "C" {
 #define EIC_EOVERFLOW 4 /* the largest shortest distance plus the largest weight reaches 2^32-1 */
 #define EIC_ETIMEOUT 5  /* a bounded device-side wait (grid barrier) ran out; the context stays usable */
 #define EIC_EBUSY 6     /* the object is in use by another call */
+#define EIC_ESIZE 7     /* the graph exceeds the fixed limits of eic_sssp_noalloc */
 
 /* Opaque, device-resident graph owned by the library (create/destroy). */
 typedef struct eic_graph eic_graph;
@@ -184,6 +185,44 @@ int eic_sssp(const eic_graph* g, uint32_t source, uint32_t* dist, uint32_t* pare
  */
 int eic_sssp_batch(const eic_graph* const* graphs, const uint32_t* sources, uint32_t num_queries,
                    uint32_t* const* dists, const eic_params* params, int* statuses, void* stream);
+
+/*
+ * Allocation-free single-source query. The paper has no counterpart: this
+ * entry point exists for callers that cannot call cudaMalloc at query time,
+ * for example a serving process that plans its whole device-memory budget up
+ * front and treats any allocation as a failure, code running inside another
+ * framework's memory pool, or a latency-critical loop that cannot afford
+ * cudaMalloc's implicit device synchronisation.
+ *
+ * Same result as eic_sssp (exact distances, paper's default parameters), but
+ * the query's scratch (frontier queues, settled list, statistics, tasks,
+ * control block) lives in one fixed-size device array inside libeic instead of
+ * the graph's workspace. That array (about 13 MB) is held on every GPU where
+ * the library is loaded, until the process exits. The call allocates nothing:
+ * no cudaMalloc, cudaFree or allocating library routine; the caller supplies
+ * the graph (created beforehand with eic_graph_create) and the output buffer.
+ *   source   0 <= source < n.
+ *   dist     device array of n uint32, caller-owned.
+ *   stream   the work is enqueued here; the call waits for it to finish.
+ * Limits: n <= EIC_NOALLOC_MAX_VERTICES, 2m <= EIC_NOALLOC_MAX_ENTRIES,
+ * largest weight <= EIC_NOALLOC_MAX_WEIGHT, at most EIC_NOALLOC_MAX_DEGREES
+ * distinct degrees; a larger graph returns EIC_ESIZE. A query needing more than
+ * EIC_NOALLOC_MAX_STEPS steps returns EIC_ENOMEM.
+ * The first call on a device sets up that device (looks up the scratch
+ * address and clears it); make that first call before any stream capture.
+ * Every call uses the same scratch, which keeps the previous call's contents
+ * (the call clears what must start at zero): calls whose work overlaps on the
+ * GPU (other streams, other host threads) race and must be serialised by the
+ * caller.
+ * Errors: EIC_EINVAL, EIC_ESIZE, EIC_ECUDA, EIC_EOVERFLOW, EIC_ETIMEOUT,
+ * EIC_ENOMEM (step limit).
+ */
+#define EIC_NOALLOC_MAX_VERTICES (1u << 18)
+#define EIC_NOALLOC_MAX_ENTRIES (1u << 22)
+#define EIC_NOALLOC_MAX_WEIGHT 65535u
+#define EIC_NOALLOC_MAX_DEGREES 4096u
+#define EIC_NOALLOC_MAX_STEPS (1u << 14)
+int eic_sssp_noalloc(const eic_graph* g, uint32_t source, uint32_t* dist, void* stream);
 
 #ifdef __cplusplus
 }

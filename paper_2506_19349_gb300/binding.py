@@ -18,12 +18,14 @@ LIB_PATH = os.path.join(_HERE, "libeic.so")
 
 EIC_INF = 0xFFFFFFFF
 RATIO_NUM = 4096
-OK, EINVAL, ENOMEM, ECUDA, EOVERFLOW, ETIMEOUT, EBUSY = range(7)
+OK, EINVAL, ENOMEM, ECUDA, EOVERFLOW, ETIMEOUT, EBUSY, ESIZE = range(8)
+NOALLOC_MAX_VERTICES = 1 << 18
 FLAG_NO_PULL = 1
 
 # Every name declared in include/eic.h.
 EXPORTS = ("eic_params_default", "eic_strerror", "eic_version", "eic_graph_create", "eic_graph_info",
-           "eic_graph_export", "eic_graph_memory", "eic_graph_destroy", "eic_sssp", "eic_sssp_batch")
+           "eic_graph_export", "eic_graph_memory", "eic_graph_destroy", "eic_sssp", "eic_sssp_batch",
+           "eic_sssp_noalloc")
 
 
 class Params(ctypes.Structure):
@@ -88,6 +90,8 @@ def load_library(path: str | None = None):
         L.eic_sssp.restype = c_int
         L.eic_sssp_batch.argtypes = [ctypes.POINTER(vp), vp, u32, ctypes.POINTER(vp), ctypes.POINTER(Params), vp, vp]
         L.eic_sssp_batch.restype = c_int
+        L.eic_sssp_noalloc.argtypes = [vp, u32, vp, vp]
+        L.eic_sssp_noalloc.restype = c_int
         _lib = L
         return L
 
@@ -244,3 +248,11 @@ def sssp_batch(graphs, sources, dists, params: Params | None = None, stream=None
 
 def to_host_u32(t) -> np.ndarray:
     return t.detach().cpu().numpy().view(np.uint32)
+
+
+def sssp_noalloc(graph: Graph, source: int, dist, stream=None) -> int:
+    """eic_sssp_noalloc: the query with libeic's fixed scratch instead of the
+    graph's workspace, for callers that cannot allocate device memory at query
+    time. dist is a caller-provided int32 CUDA tensor of n elements. Returns the
+    status code."""
+    return load_library().eic_sssp_noalloc(graph.handle, int(source), dist.data_ptr(), _stream_ptr(stream))

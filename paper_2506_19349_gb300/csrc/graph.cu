@@ -543,6 +543,7 @@ const char* eic_strerror(int status) {
     case EIC_EOVERFLOW: return "distance overflow (max distance + max weight >= 2^32-1)";
     case EIC_ETIMEOUT: return "device wait timed out";
     case EIC_EBUSY: return "busy";
+    case EIC_ESIZE: return "graph exceeds the limits of the allocation-free entry point";
     default: return "unknown status";
   }
 }

@@ -1416,3 +1416,150 @@ int eic_sssp_batch(const eic_graph* const* graphs, const uint32_t* sources, uint
 }
 
 }  // extern "C"
+
+// ------------------------------------------------ allocation-free entry point
+//
+// The query scratch of eic_sssp_noalloc: one file-scope device array carved
+// into the workspace arrays of a graph with at most kNaN vertices, kNaE
+// adjacency entries, weights below 2^16 and kNaD distinct degrees. Every GPU
+// that loads the library holds it until the process exits.
+namespace {
+
+constexpr uint64_t kNaN = EIC_NOALLOC_MAX_VERTICES;
+constexpr uint64_t kNaE = EIC_NOALLOC_MAX_ENTRIES;
+constexpr uint64_t kNaD = EIC_NOALLOC_MAX_DEGREES;
+constexpr uint64_t kNaS = EIC_NOALLOC_MAX_STEPS;
+constexpr uint32_t kNaRingBits = 16;  // 2^16 > EIC_NOALLOC_MAX_WEIGHT
+constexpr uint64_t kNaTasks = kNaE / kHeavyMinFloor + 2;
+
+constexpr uint64_t na_align(uint64_t x) { return (x + 255) & ~255ull; }
+constexpr uint64_t kNaStamp = 0;
+constexpr uint64_t kNaCursor = kNaStamp + na_align(kNaN * 4);
+constexpr uint64_t kNaQ0 = kNaCursor + na_align(kNaN * 4);
+constexpr uint64_t kNaQ1 = kNaQ0 + na_align(kNaN * 4);
+constexpr uint64_t kNaSid = kNaQ1 + na_align(kNaN * 4);
+constexpr uint64_t kNaSd = kNaSid + na_align((kNaN + 2) * 4);
+constexpr uint64_t kNaScur = kNaSd + na_align((kNaN + 2) * 4);
+constexpr uint64_t kNaTouched = kNaScur + na_align((kNaN + 2) * 4);
+constexpr uint64_t kNaSbits = kNaTouched + na_align((kNaN + 1) * 4);
+constexpr uint64_t kNaHist = kNaSbits + na_align((kNaN / 32 + 2) * 4);
+constexpr uint64_t kNaRing = kNaHist + na_align(kNaD * 4);
+constexpr uint64_t kNaTaskOff = kNaRing + na_align((1ull << kNaRingBits) * 8);
+constexpr uint64_t kNaStepUb = kNaTaskOff + na_align(kNaTasks * sizeof(Task));
+constexpr uint64_t kNaStepOff = kNaStepUb + na_align((kNaS + 2) * 8);
+constexpr uint64_t kNaCtl = kNaStepOff + na_align((kNaS + 2) * 4);
+constexpr uint64_t kNaBytes = kNaCtl + na_align(sizeof(Ctl));
+
+static __device__ __align__(256) unsigned char g_na_scratch[kNaBytes];
+
+struct NaDevice {
+  bool ready = false;
+  unsigned char* base = nullptr;  // device address of g_na_scratch on this device
+  int grid = 0;
+  uint32_t round_base = 0;
+};
+NaDevice g_na[kMaxDevices];
+std::mutex g_na_mu;
+
+// Once per device, with that device current: the scratch's device address
+// (the symbol's host-side name is not a device pointer), cleared stamps and
+// control block, and the cooperative grid shape.
+int na_setup(NaDevice& d, cudaStream_t st) {
+  void* ptr = nullptr;
+  EIC_CUDA_TRY(cudaGetSymbolAddress(&ptr, g_na_scratch));
+  if (!ptr) return EIC_ECUDA;
+  int dev = 0, sms = 0, per_sm = 0, coop = 0;
+  EIC_CUDA_TRY(cudaGetDevice(&dev));
+  EIC_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  EIC_CUDA_TRY(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
+  if (!coop) return EIC_ECUDA;
+  EIC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_eic, kDefaultBlock, 0));
+  if (per_sm < 1) return EIC_ECUDA;
+  unsigned char* base = (unsigned char*)ptr;
+  EIC_CUDA_TRY(cudaMemsetAsync(base + kNaStamp, 0, kNaN * 4, st));
+  EIC_CUDA_TRY(cudaMemsetAsync(base + kNaCtl, 0, sizeof(Ctl), st));
+  EIC_CUDA_TRY(cudaStreamSynchronize(st));
+  d.base = base;
+  d.grid = sms * per_sm;
+  d.round_base = 0;
+  d.ready = true;
+  return EIC_OK;
+}
+
+}  // namespace
+
+extern "C" int eic_sssp_noalloc(const eic_graph* gc, uint32_t source, uint32_t* dist, void* stream) {
+  if (!gc || !dist) return EIC_EINVAL;
+  const DevGraph& G = gc->dg;
+  if (source >= G.n) return EIC_EINVAL;
+  if (G.n > kNaN || G.two_m > kNaE || G.maxw > EIC_NOALLOC_MAX_WEIGHT || G.D > kNaD) return EIC_ESIZE;
+  cudaStream_t st = (cudaStream_t)stream;
+  std::lock_guard<std::mutex> lock(g_na_mu);
+  DeviceGuard guard(gc->device);
+  if (!guard.ok || gc->device < 0 || gc->device >= kMaxDevices) return EIC_ECUDA;
+  NaDevice& nd = g_na[gc->device];
+  int rc;
+  if (!nd.ready && (rc = na_setup(nd, st))) return rc;
+  if (G.two_m == 0) {  // no edges: only the source is reachable
+    EIC_CUDA_TRY(cudaMemsetAsync(dist, 0xFF, (uint64_t)G.n * 4, st));
+    EIC_CUDA_TRY(cudaMemsetAsync(dist + source, 0, 4, st));
+    EIC_CUDA_TRY(cudaStreamSynchronize(st));
+    return EIC_OK;
+  }
+  unsigned char* b = nd.base;
+  Ctl* ctl = (Ctl*)(b + kNaCtl);
+  if (nd.round_base > (1u << 30)) {  // keep stamp ids far from wrapping
+    EIC_CUDA_TRY(cudaMemsetAsync(b + kNaStamp, 0, kNaN * 4, st));
+    EIC_CUDA_TRY(cudaMemsetAsync(&ctl->round_base, 0, 4, st));
+  }
+  KArgs A;
+  A.G = G;
+  A.dist = dist;
+  A.stamp = (uint32_t*)(b + kNaStamp);
+  A.cursor = (uint32_t*)(b + kNaCursor);
+  A.q0 = (uint32_t*)(b + kNaQ0);
+  A.q1 = (uint32_t*)(b + kNaQ1);
+  A.sid = (uint32_t*)(b + kNaSid);
+  A.sd = (uint32_t*)(b + kNaSd);
+  A.scur = (uint32_t*)(b + kNaScur);
+  A.touched = (uint32_t*)(b + kNaTouched);
+  A.sbits = (uint32_t*)(b + kNaSbits);
+  A.hist = (uint32_t*)(b + kNaHist);
+  A.ring = (unsigned long long*)(b + kNaRing);
+  A.tasks = (Task*)(b + kNaTaskOff);
+  A.step_ub = (int64_t*)(b + kNaStepUb);
+  A.step_off = (uint32_t*)(b + kNaStepOff);
+  A.trace = nullptr;
+  A.ctl = ctl;
+  A.status_out = nullptr;
+  A.s = source;
+  A.alpha = 3;
+  A.beta = 0.9;
+  A.st_num = 1024;
+  A.gap_shift = 0;
+  A.heavy_min = kDefaultHeavyMin;
+  A.max_spin = 1ull << kDefaultSpinLog2;
+  A.flags = 0;
+  A.ring_mask = (1u << kNaRingBits) - 1u;
+  A.ring_shift = 0;
+  A.task_cap = (uint32_t)kNaTasks;
+  A.step_cap = (uint32_t)kNaS;
+  A.trace_cap = 0;
+  A.timeline = nullptr;
+  A.timeline_cap = 0;
+  EIC_CUDA_TRY(cudaMemsetAsync(dist, 0xFF, (uint64_t)G.n * 4, st));
+  EIC_CUDA_TRY(cudaMemsetAsync(A.sbits, 0, ((uint64_t)G.n / 32 + 2) * 4, st));
+  k_init<<<64, 256, 0, st>>>(A);
+  EIC_CUDA_TRY(cudaGetLastError());
+  void* args[] = {&A};
+  EIC_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)k_eic, dim3(nd.grid), dim3(kDefaultBlock), args, 0, st));
+  struct {
+    int status;
+    uint32_t round_base;
+  } h = {0, 0};
+  EIC_CUDA_TRY(cudaMemcpyAsync(&h.status, &ctl->status, sizeof(int), cudaMemcpyDeviceToHost, st));
+  EIC_CUDA_TRY(cudaMemcpyAsync(&h.round_base, &ctl->round_base, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+  EIC_CUDA_TRY(cudaStreamSynchronize(st));
+  nd.round_base = h.round_base;
+  return h.status;
+}

@@ -41,7 +41,7 @@ def test_host_only_calls(lib):
     p = binding.default_params()
     assert (p.alpha, p.beta, p.st_num, p.gap_shift, p.flags) == (3, 0.9, 1024, 0, 0)
     assert lib.eic_params_default(None) == binding.EINVAL
-    for code in range(7):
+    for code in range(8):
         assert lib.eic_strerror(code)
     assert lib.eic_version() >= 100
     out = ctypes.c_void_p()
