@@ -21,18 +21,23 @@
   } while (0)
 
 // Read-only view of a device-resident graph (preprocessing of Section 4.1).
+// Vertices have internal ids 0..ni-1: the non-isolated vertices ordered by
+// (degree descending, original id); orig2int/int2orig translate.
 struct DevGraph {
-  uint32_t n;
+  uint32_t n;             // vertices in the caller's numbering
+  uint32_t ni;            // internal vertices (degree >= 1)
+  const uint32_t* orig2int;  // [n] internal id, or 0xFFFFFFFF for an isolated vertex
+  const uint32_t* int2orig;  // [ni]
   uint64_t two_m;         // directed entries, sum of degrees
   uint64_t m;             // undirected edges
-  const uint32_t* row;    // [n + 1] row offsets (2m < 2^32)
+  const uint32_t* row;    // [ni + 1] row offsets (2m < 2^32)
   const uint2* adj;       // [two_m] {neighbour, weight}, rows sorted by (weight, neighbour)
   const uint32_t* drank;  // [max_deg + 1] degree -> rank among distinct degrees (present ones)
   const uint32_t* dvals;  // [D] distinct degrees >= 1, ascending
   const uint32_t* dcnt0;  // [D] number of vertices with degree dvals[r]
   uint32_t D;
   const uint32_t* rtow;   // [EIC_RATIO_NUM] maxW(G, i / (RATIO_NUM - 1))
-  const uint2* nz;        // [nz_count] {vertex, smallest row weight} for degree >= 1, by (weight, vertex)
+  const uint2* nz;        // [nz_count = ni] {internal id, smallest row weight}, by (weight, id)
   uint32_t nz_count;
   const uint32_t* nz_lt;  // [nz_lt_len] nz_lt[t] = number of nz entries with smallest weight < t
   uint32_t nz_lt_len;

@@ -14,7 +14,9 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
 #include <new>
+#include <vector>
 
 #include "graph.h"
 #include "radix.cuh"
@@ -105,18 +107,47 @@ __global__ void k_degrees(const uint64_t* __restrict__ ukeys, const uint32_t* __
   }
 }
 
-// Both directions of pair i at positions 2i, 2i+1; sort key (row, weight).
+// Both directions of pair i at positions 2i, 2i+1 in internal ids; sort key (row, weight).
 __global__ void k_emit(const uint64_t* __restrict__ ukeys, const uint32_t* __restrict__ uw, uint64_t m, int vbits,
-                       int wbits, uint64_t* keys, uint32_t* vals) {
+                       const uint32_t* __restrict__ orig2int, int wbits, uint64_t* keys, uint32_t* vals) {
   const uint64_t vmask = (1ull << vbits) - 1;
   for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < m; i += (uint64_t)gridDim.x * blockDim.x) {
     uint64_t k = ukeys[i];
-    uint32_t a = (uint32_t)(k >> vbits), b = (uint32_t)(k & vmask), w = uw[i];
+    uint32_t a = orig2int[k >> vbits], b = orig2int[k & vmask], w = uw[i];
     keys[2 * i] = ((uint64_t)a << wbits) | w;
     vals[2 * i] = b;
     keys[2 * i + 1] = ((uint64_t)b << wbits) | w;
     vals[2 * i + 1] = a;
   }
+}
+
+// key of non-isolated vertex v: (maxdeg - deg(v), v), at its compacted position
+__global__ void k_relabel_keys(const uint32_t* __restrict__ deg, const uint32_t* __restrict__ flags,
+                               const uint64_t* __restrict__ pos, uint32_t n, uint32_t maxdeg, int vbits,
+                               uint64_t* keys) {
+  for (uint64_t v = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; v < n; v += (uint64_t)gridDim.x * blockDim.x)
+    if (flags[v]) keys[pos[v]] = ((uint64_t)(maxdeg - deg[v]) << vbits) | v;
+}
+
+__global__ void k_relabel_maps(const uint64_t* __restrict__ keys, uint32_t ni, int vbits, uint32_t* int2orig,
+                               uint32_t* orig2int) {
+  const uint64_t vmask = (1ull << vbits) - 1;
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < ni; i += gridDim.x * blockDim.x) {
+    const uint32_t v = (uint32_t)(keys[i] & vmask);
+    int2orig[i] = v;
+    orig2int[v] = i;
+  }
+}
+
+__global__ void k_gather_u32(const uint32_t* __restrict__ src, const uint32_t* __restrict__ idx, uint32_t cnt,
+                             uint32_t* out) {
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += gridDim.x * blockDim.x) out[i] = src[idx[i]];
+}
+
+// nz[i] = {i, smallest weight of row i} for every internal vertex
+__global__ void k_nz_fill(const uint32_t* __restrict__ row, const uint2* __restrict__ adj, uint32_t ni, uint2* nz) {
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < ni; i += gridDim.x * blockDim.x)
+    nz[i] = make_uint2(i, adj[row[i]].y);
 }
 
 __global__ void k_pack_adj(const uint64_t* __restrict__ keys, const uint32_t* __restrict__ vals, uint64_t E,
@@ -220,13 +251,6 @@ __global__ void k_flag_nonzero(const uint32_t* __restrict__ deg, uint32_t n, uin
     flags[v] = deg[v] ? 1u : 0u;
 }
 
-// nz[k] = {v, smallest weight of v's row} for the k-th vertex with degree >= 1
-__global__ void k_scatter_nz(const uint32_t* __restrict__ flags, const uint64_t* __restrict__ pos,
-                             const uint32_t* __restrict__ row, const uint2* __restrict__ adj, uint32_t n, uint2* nz) {
-  for (uint64_t v = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; v < n; v += (uint64_t)gridDim.x * blockDim.x)
-    if (flags[v]) nz[pos[v]] = make_uint2((uint32_t)v, adj[row[v]].y);
-}
-
 // Temporary device allocations released on every exit path.
 struct Temps {
   void* p[24];
@@ -282,6 +306,8 @@ void graph_free_arrays(eic_graph* g) {
   cudaFree(g->rtow);
   cudaFree(g->nz);
   cudaFree(g->nz_lt);
+  cudaFree(g->orig2int);
+  cudaFree(g->int2orig);
 }
 
 int build(eic_graph* g, const uint32_t* src, const uint32_t* dst, const uint32_t* w, uint64_t T, uint32_t n,
@@ -368,27 +394,68 @@ int build(eic_graph* g, const uint32_t* src, const uint32_t* dst, const uint32_t
   }
   const uint64_t E = 2 * m;
 
-  // 3. degrees, weight range, row offsets
+  // 3. degrees in original ids, weight range
   uint32_t* deg;
   TRY(tmp.alloc(&deg, (uint64_t)n + 1));
   EIC_CUDA_TRY(cudaMemsetAsync(deg, 0, ((uint64_t)n + 1) * 4, st));
   if (m > 0) k_degrees<<<grid_for(m), kThreads, 0, st>>>(ukeys, uw, m, vbits, deg, small + 1, small + 2);
-  TRY(galloc(g, &g->row, (uint64_t)n + 1));
-  {
-    uint64_t* row64;
-    TRY(tmp.alloc(&row64, (uint64_t)n + 1));
-    TRY(exclusive_scan<uint32_t>(deg, n, row64, scan_scratch, st));
-    k_narrow<<<grid_for((uint64_t)n + 1), kThreads, 0, st>>>(row64, (uint64_t)n + 1, g->row);
-    EIC_CUDA_TRY(cudaGetLastError());
-    EIC_CUDA_TRY(cudaStreamSynchronize(st));
-    tmp.release(row64);
-  }
+  k_max_u32<<<grid_for(n), kThreads, 0, st>>>(deg, n, small + 3);
+  EIC_CUDA_TRY(cudaGetLastError());
   EIC_CUDA_TRY(cudaMemcpyAsync(hs, small, sizeof(hs), cudaMemcpyDeviceToHost, st));
   EIC_CUDA_TRY(cudaStreamSynchronize(st));
   const uint32_t maxw = m ? hs[1] : 0, minw = m ? hs[2] : 0;
+  const uint32_t maxdeg = hs[3];
   const int wbits = bits_for(maxw);
 
-  // 4. both directions, stable sort by (row, weight) -> rows in (weight, neighbour) order
+  // 3b. internal ids: the non-isolated vertices ordered by (degree descending,
+  // original id), so that the most-touched vertices share cache lines
+  uint32_t ni = 0;
+  TRY(galloc(g, &g->orig2int, n));
+  EIC_CUDA_TRY(cudaMemsetAsync(g->orig2int, 0xFF, (uint64_t)n * 4, st));
+  {
+    uint32_t* flags;
+    uint64_t* pos;
+    TRY(tmp.alloc(&flags, n));
+    TRY(tmp.alloc(&pos, (uint64_t)n + 1));
+    k_flag_nonzero<<<grid_for(n), kThreads, 0, st>>>(deg, n, flags);
+    TRY(exclusive_scan<uint32_t>(flags, n, pos, scan_scratch, st));
+    uint64_t c = 0;
+    EIC_CUDA_TRY(cudaMemcpyAsync(&c, pos + n, 8, cudaMemcpyDeviceToHost, st));
+    EIC_CUDA_TRY(cudaStreamSynchronize(st));
+    ni = (uint32_t)c;
+    TRY(galloc(g, &g->int2orig, ni));
+    uint64_t *rk0, *rk1;
+    TRY(tmp.alloc(&rk0, ni));
+    TRY(tmp.alloc(&rk1, ni));
+    const int dbits = bits_for(maxdeg);
+    k_relabel_keys<<<grid_for(n), kThreads, 0, st>>>(deg, flags, pos, n, maxdeg, vbits, rk0);
+    bool alt = false;
+    TRY(radix_sort(rk0, nullptr, rk1, nullptr, ni, dbits + vbits, hist_scratch, st, &alt));
+    k_relabel_maps<<<grid_for(ni), kThreads, 0, st>>>(alt ? rk1 : rk0, ni, vbits, g->int2orig, g->orig2int);
+    EIC_CUDA_TRY(cudaGetLastError());
+    EIC_CUDA_TRY(cudaStreamSynchronize(st));
+    tmp.release(rk0);
+    tmp.release(rk1);
+    tmp.release(flags);
+    tmp.release(pos);
+  }
+  const int ibits = bits_for(ni > 1 ? ni - 1 : 1);
+  TRY(galloc(g, &g->row, (uint64_t)ni + 1));
+  {
+    uint32_t* deg_int;
+    uint64_t* row64;
+    TRY(tmp.alloc(&deg_int, (uint64_t)ni + 1));
+    TRY(tmp.alloc(&row64, (uint64_t)ni + 1));
+    k_gather_u32<<<grid_for(ni), kThreads, 0, st>>>(deg, g->int2orig, ni, deg_int);
+    TRY(exclusive_scan<uint32_t>(deg_int, ni, row64, scan_scratch, st));
+    k_narrow<<<grid_for((uint64_t)ni + 1), kThreads, 0, st>>>(row64, (uint64_t)ni + 1, g->row);
+    EIC_CUDA_TRY(cudaGetLastError());
+    EIC_CUDA_TRY(cudaStreamSynchronize(st));
+    tmp.release(row64);
+    tmp.release(deg_int);
+  }
+
+  // 4. both directions in internal ids, stable sort by (row, weight): rows in weight order
   TRY(galloc(g, &g->adj, E));
   if (E > 0) {
     uint64_t *ek0, *ek1;
@@ -397,9 +464,9 @@ int build(eic_graph* g, const uint32_t* src, const uint32_t* dst, const uint32_t
     TRY(tmp.alloc(&ev0, E));
     TRY(tmp.alloc(&ek1, E));
     TRY(tmp.alloc(&ev1, E));
-    k_emit<<<grid_for(m), kThreads, 0, st>>>(ukeys, uw, m, vbits, wbits, ek0, ev0);
+    k_emit<<<grid_for(m), kThreads, 0, st>>>(ukeys, uw, m, vbits, g->orig2int, wbits, ek0, ev0);
     bool alt = false;
-    TRY(radix_sort(ek0, ev0, ek1, ev1, E, vbits + wbits, hist_scratch, st, &alt));
+    TRY(radix_sort(ek0, ev0, ek1, ev1, E, ibits + wbits, hist_scratch, st, &alt));
     k_pack_adj<<<grid_for(E), kThreads, 0, st>>>(alt ? ek1 : ek0, alt ? ev1 : ev0, E, wbits, g->adj);
     EIC_CUDA_TRY(cudaGetLastError());
     EIC_CUDA_TRY(cudaStreamSynchronize(st));
@@ -430,10 +497,6 @@ int build(eic_graph* g, const uint32_t* src, const uint32_t* dst, const uint32_t
   tmp.release(uw);
 
   // 5b. distinct-degree tables and highD(0)
-  k_max_u32<<<grid_for(n), kThreads, 0, st>>>(deg, n, small + 3);
-  EIC_CUDA_TRY(cudaMemcpyAsync(hs, small, sizeof(hs), cudaMemcpyDeviceToHost, st));
-  EIC_CUDA_TRY(cudaStreamSynchronize(st));
-  const uint32_t maxdeg = hs[3];
   const uint32_t hlen = maxdeg + 1;
   uint32_t D = 0;
   {
@@ -458,32 +521,22 @@ int build(eic_graph* g, const uint32_t* src, const uint32_t* dst, const uint32_t
     EIC_CUDA_TRY(cudaGetLastError());
   }
 
-  // 5c. non-isolated vertices with their smallest weight
-  uint32_t nzc = 0, nz_lt_len = 0;
+  // 5c. every internal vertex with its smallest weight, ordered by (smallest
+  // weight, id): the vertices a pull can touch (smallest weight below a bound)
+  // form a prefix, located with nz_lt
+  uint32_t nz_lt_len = 0;
   {
-    uint32_t* flags;
-    uint64_t* pos;
-    TRY(tmp.alloc(&flags, n));
-    TRY(tmp.alloc(&pos, (uint64_t)n + 1));
-    k_flag_nonzero<<<grid_for(n), kThreads, 0, st>>>(deg, n, flags);
-    TRY(exclusive_scan<uint32_t>(flags, n, pos, scan_scratch, st));
-    uint64_t c = 0;
-    EIC_CUDA_TRY(cudaMemcpyAsync(&c, pos + n, 8, cudaMemcpyDeviceToHost, st));
-    EIC_CUDA_TRY(cudaStreamSynchronize(st));
-    nzc = (uint32_t)c;
-    TRY(galloc(g, &g->nz, nzc));
-    k_scatter_nz<<<grid_for(n), kThreads, 0, st>>>(flags, pos, g->row, g->adj, n, g->nz);
+    TRY(galloc(g, &g->nz, ni));
+    k_nz_fill<<<grid_for(ni), kThreads, 0, st>>>(g->row, g->adj, ni, g->nz);
     EIC_CUDA_TRY(cudaGetLastError());
-    // order by (smallest weight, vertex): the vertices a pull can touch (smallest
-    // weight below a bound) then form a prefix, located with nz_lt
-    if (nzc > 1) {
+    if (ni > 1) {
       uint64_t *kk0, *kk1;
-      TRY(tmp.alloc(&kk0, nzc));
-      TRY(tmp.alloc(&kk1, nzc));
-      k_nz_keys<<<grid_for(nzc), kThreads, 0, st>>>(g->nz, nzc, vbits, kk0);
+      TRY(tmp.alloc(&kk0, ni));
+      TRY(tmp.alloc(&kk1, ni));
+      k_nz_keys<<<grid_for(ni), kThreads, 0, st>>>(g->nz, ni, ibits, kk0);
       bool alt = false;
-      TRY(radix_sort(kk0, nullptr, kk1, nullptr, nzc, vbits + wbits, hist_scratch, st, &alt));
-      k_nz_from_keys<<<grid_for(nzc), kThreads, 0, st>>>(alt ? kk1 : kk0, nzc, vbits, g->nz);
+      TRY(radix_sort(kk0, nullptr, kk1, nullptr, ni, ibits + wbits, hist_scratch, st, &alt));
+      k_nz_from_keys<<<grid_for(ni), kThreads, 0, st>>>(alt ? kk1 : kk0, ni, ibits, g->nz);
       EIC_CUDA_TRY(cudaGetLastError());
       EIC_CUDA_TRY(cudaStreamSynchronize(st));
       tmp.release(kk0);
@@ -491,7 +544,7 @@ int build(eic_graph* g, const uint32_t* src, const uint32_t* dst, const uint32_t
     }
     nz_lt_len = (maxw < 65535u ? maxw + 1 : 65536u) + 1;
     TRY(galloc(g, &g->nz_lt, nz_lt_len));
-    k_nz_lt<<<grid_for(nzc + 1), kThreads, 0, st>>>(g->nz, nzc, nz_lt_len, g->nz_lt);
+    k_nz_lt<<<grid_for((uint64_t)ni + 1), kThreads, 0, st>>>(g->nz, ni, nz_lt_len, g->nz_lt);
     EIC_CUDA_TRY(cudaGetLastError());
   }
   EIC_CUDA_TRY(cudaMemcpyAsync(hs, small, sizeof(hs), cudaMemcpyDeviceToHost, st));
@@ -499,6 +552,9 @@ int build(eic_graph* g, const uint32_t* src, const uint32_t* dst, const uint32_t
 
   DevGraph& dg = g->dg;
   dg.n = n;
+  dg.ni = ni;
+  dg.orig2int = g->orig2int;
+  dg.int2orig = g->int2orig;
   dg.two_m = E;
   dg.m = m;
   dg.row = g->row;
@@ -509,7 +565,7 @@ int build(eic_graph* g, const uint32_t* src, const uint32_t* dst, const uint32_t
   dg.D = D;
   dg.rtow = g->rtow;
   dg.nz = g->nz;
-  dg.nz_count = nzc;
+  dg.nz_count = ni;
   dg.nz_lt = g->nz_lt;
   dg.nz_lt_len = nz_lt_len;
   dg.maxw = maxw;
@@ -594,33 +650,45 @@ int eic_graph_export(const eic_graph* g, uint64_t* row_ptr, uint32_t* nbr, uint3
   cudaGetDevice(&dev);
   cudaSetDevice(g->device);
   int rc = EIC_OK;
-  const uint64_t E = g->dg.two_m;
-  if (row_ptr) {
-    const uint64_t cnt = (uint64_t)g->dg.n + 1;
-    uint32_t* h = (uint32_t*)malloc(cnt * 4);
-    if (!h) {
-      rc = EIC_ENOMEM;
-    } else {
-      if (cudaMemcpy(h, g->row, cnt * 4, cudaMemcpyDeviceToHost) != cudaSuccess) rc = EIC_ECUDA;
-      for (uint64_t i = 0; rc == EIC_OK && i < cnt; ++i) row_ptr[i] = h[i];
-      free(h);
-    }
-  }
-  if ((nbr || w) && E > 0 && rc == EIC_OK) {
-    uint2* h = (uint2*)malloc(E * sizeof(uint2));
-    if (!h) {
-      rc = EIC_ENOMEM;
-    } else {
-      if (cudaMemcpy(h, g->adj, E * sizeof(uint2), cudaMemcpyDeviceToHost) != cudaSuccess) rc = EIC_ECUDA;
-      for (uint64_t i = 0; rc == EIC_OK && i < E; ++i) {
-        if (nbr) nbr[i] = h[i].x;
-        if (w) w[i] = h[i].y;
+  const uint64_t n = g->dg.n, ni = g->dg.ni, E = g->dg.two_m;
+  uint32_t* o2i = (uint32_t*)malloc((n ? n : 1) * 4);
+  uint32_t* i2o = (uint32_t*)malloc((ni ? ni : 1) * 4);
+  uint32_t* row = (uint32_t*)malloc((ni + 1) * 4);
+  uint2* adj = (nbr || w) ? (uint2*)malloc((E ? E : 1) * sizeof(uint2)) : nullptr;
+  if (!o2i || !i2o || !row || ((nbr || w) && !adj)) rc = EIC_ENOMEM;
+  if (rc == EIC_OK && (cudaMemcpy(o2i, g->orig2int, n * 4, cudaMemcpyDeviceToHost) != cudaSuccess ||
+                       cudaMemcpy(i2o, g->int2orig, ni * 4, cudaMemcpyDeviceToHost) != cudaSuccess ||
+                       cudaMemcpy(row, g->row, (ni + 1) * 4, cudaMemcpyDeviceToHost) != cudaSuccess ||
+                       (adj && E && cudaMemcpy(adj, g->adj, E * sizeof(uint2), cudaMemcpyDeviceToHost) != cudaSuccess)))
+    rc = EIC_ECUDA;
+  if (rc == EIC_OK) {
+    // rows in original vertex order, each sorted by (weight, original neighbour)
+    uint64_t off = 0;
+    std::vector<uint64_t> tmpk;
+    for (uint64_t u = 0; u < n; ++u) {
+      if (row_ptr) row_ptr[u] = off;
+      const uint32_t i = o2i[u];
+      if (i == 0xFFFFFFFFu) continue;
+      const uint32_t b = row[i], e = row[i + 1];
+      if (adj) {
+        tmpk.resize(e - b);
+        for (uint32_t k = b; k < e; ++k) tmpk[k - b] = ((uint64_t)adj[k].y << 32) | i2o[adj[k].x];
+        std::sort(tmpk.begin(), tmpk.end());
+        for (uint32_t k = 0; k < e - b; ++k) {
+          if (nbr) nbr[off + k] = (uint32_t)tmpk[k];
+          if (w) w[off + k] = (uint32_t)(tmpk[k] >> 32);
+        }
       }
-      free(h);
+      off += e - b;
     }
+    if (row_ptr) row_ptr[n] = off;
   }
   if (rtow && rc == EIC_OK && cudaMemcpy(rtow, g->rtow, EIC_RATIO_NUM * 4, cudaMemcpyDeviceToHost) != cudaSuccess)
     rc = EIC_ECUDA;
+  free(o2i);
+  free(i2o);
+  free(row);
+  free(adj);
   (void)cudaGetLastError();
   cudaSetDevice(dev);
   return rc;

@@ -19,6 +19,7 @@ struct Ctl {
   // published by the step-boundary block, read by every block after a barrier
   int64_t lb, ub, st, lb0;
   uint32_t step, done;
+  uint32_t s_int;  // internal id of the source (0xFFFFFFFF: isolated source)
   uint32_t push_beg, push_end;  // settled-list range pushed in round 1
   uint32_t pull_on, pull_cnt, extra_s;
   uint32_t step_off_cur;  // settled-list offset where the current step's vertices start
@@ -40,7 +41,6 @@ struct Ctl {
   uint32_t acc_maxd;
   unsigned long long acc_deg;
   uint32_t acc_any;
-  uint32_t round_base;  // stamp id of the last round of the previous query
   unsigned long long cnt_rounds, cnt_frontier, cnt_trav, cnt_pulls, cnt_improved, cnt_heavy, cnt_pitems;
   GridBarrier bar;
   int status;
@@ -48,7 +48,8 @@ struct Ctl {
 
 struct Workspace {
   uint32_t n = 0;
-  uint32_t* stamp = nullptr;
+  uint32_t* idist = nullptr;  // distances in internal ids
+  uint32_t* fbits = nullptr;  // two frontier-insertion bitmaps
   uint32_t* q[2] = {nullptr, nullptr};
   uint32_t* sid = nullptr;   // settled list: vertex
   uint32_t* sd = nullptr;    // settled list: final distance
@@ -68,7 +69,6 @@ struct Workspace {
   uint32_t ring_bits = 0, ring_shift = 0;
   uint32_t task_cap = 0, step_cap = 0;
   uint64_t bytes = 0;
-  uint32_t host_round_base = 0;
   int grid = 0, block = 0;  // cached cooperative launch shape
 };
 
@@ -83,6 +83,8 @@ struct eic_graph {
   uint32_t* rtow = nullptr;
   uint2* nz = nullptr;
   uint32_t* nz_lt = nullptr;
+  uint32_t* orig2int = nullptr;
+  uint32_t* int2orig = nullptr;
   uint64_t bytes = 0;
   Workspace ws;
   std::mutex mu;

@@ -5,8 +5,11 @@
 // Algorithm 1), as one persistent cooperative kernel on sm_103a.
 //
 // Device layout per query (workspace, reused across queries of one graph):
-//   dist[n]      caller's buffer, u32, +inf = 0xFFFFFFFF, updated by atomicMin
-//   stamp[n]     round id of the last frontier insertion (the SAP of Algorithm 1)
+//   dist[ni]     distances in internal ids (non-isolated vertices by degree,
+//                densest first), u32, +inf = 0xFFFFFFFF, updated by atomicMin;
+//                copied to the caller's buffer in the original numbering at the end
+//   fbits[2][n]  frontier bitmaps by round parity: the SAP of Algorithm 1 inserts a
+//                vertex into the next frontier only if its bit was clear
 //   cursor[n]    where the last window relaxed from a vertex ended (offset in its row)
 //   q[2][n]      frontier queues, one per round parity
 //   sid/sd/scur  settled list in settling order (vertex, final distance, window
@@ -45,8 +48,10 @@ constexpr int kShRing = 2048;
 
 struct KArgs {
   DevGraph G;
-  uint32_t* dist;
-  uint32_t* stamp;
+  uint32_t* dist;  // internal ids
+  uint32_t* out;   // caller's buffer, original ids
+  uint32_t* fbits;  // two bitmaps of fwords words
+  uint32_t fwords;
   uint32_t* cursor;
   uint32_t* q0;
   uint32_t* q1;
@@ -80,6 +85,7 @@ struct KArgs {
 constexpr uint32_t kMaxBlock = 512;
 constexpr uint32_t kMaxWarps = kMaxBlock / 32;
 constexpr uint32_t kTaskLen = 64;     // adjacency entries per grid task
+constexpr uint32_t kCursorMin = 16;   // rows longer than this keep a window cursor
 constexpr uint32_t kStageT = 1024;    // tasks staged per block
 constexpr uint32_t kStageQ = 4096;    // next-frontier appends staged per block
 constexpr uint32_t kStageF = 4096;    // settled-list appends staged per block
@@ -125,7 +131,7 @@ union PhaseScr {
 // Control values every block holds between barriers.
 struct Local {
   int64_t lb, ub, st, lb0;
-  uint32_t step, rid, qsel, cur_cnt;
+  uint32_t step, rid, qsel, cur_cnt, s_int;
   uint32_t push_beg, push_end, pull_on, pull_cnt, extra_s, step_off_cur, done;
 };
 
@@ -208,6 +214,7 @@ __device__ __forceinline__ uint32_t gallop_w(const uint2* __restrict__ adj, uint
 struct RoundCtx {
   int64_t lb, ub, ub_eff, st, lb0;
   uint32_t rid;
+  uint32_t* fbits;  // this round's insertion bitmap
   bool step1;
   uint32_t* qout;
   uint32_t* qcnt_out;
@@ -284,7 +291,11 @@ __device__ __forceinline__ void emit_tasks(const KArgs& A, const RoundCtx& R, St
 // appends go through shared memory.
 __device__ __forceinline__ void on_success(const KArgs& A, const RoundCtx& R, bool ok, uint32_t v, uint32_t nd,
                                            uint32_t old, Counters& C, Stage* T = nullptr) {
-  const bool sap = ok && (atomicExch(&A.stamp[v], R.rid) != R.rid);
+  bool sap = false;
+  if (ok) {
+    const uint32_t bit = 1u << (v & 31);
+    sap = !(atomicOr(&R.fbits[v >> 5], bit) & bit);
+  }
   const bool first = ok && old == EIC_INF;
   if (T) {
     staged_append(sap, v, &T->qn, T->qbuf, kStageQ, R.qcnt_out, R.qout);
@@ -323,7 +334,7 @@ __device__ void round_phase(const KArgs& A, const RoundCtx& R, const Local& L, R
     uint32_t u = 0, val = EIC_INF, b = 0, len = 0, mode = kModePush;
     if (i < nitems) {
       if (!round1 || i >= npp) {  // frontier vertex (or the source, once)
-        u = round1 ? A.s : __ldcg(&qin[i]);
+        u = round1 ? L.s_int : __ldcg(&qin[i]);
         const uint32_t d = __ldcg(&A.dist[u]);
         const uint32_t rb = __ldg(&A.G.row[u]), re = __ldg(&A.G.row[u + 1]);
         val = d;
@@ -333,7 +344,7 @@ __device__ void round_phase(const KArgs& A, const RoundCtx& R, const Local& L, R
           if (hi > 0) {
             b = lower_bound_w(A.G.adj, rb, re, R.lb - (int64_t)d);
             const uint32_t e = gallop_w(A.G.adj, b, re, hi);
-            __stcg(&A.cursor[u], e - rb);
+            if (re - rb > kCursorMin) __stcg(&A.cursor[u], e - rb);
             len = e - b;
           }
         }
@@ -650,7 +661,7 @@ __device__ void step_boundary(const KArgs& A, PhaseScr& P, BState& B, const Loca
     uint32_t scnt = settled_now;
     uint32_t extra = 0;
     if (k == 1 && ub == 0) {  // the source itself was not settled by the first step
-      A.sid[scnt] = A.s;
+      A.sid[scnt] = L.s_int;
       A.sd[scnt] = 0;
       A.scur[scnt] = kNone;
       ++scnt;
@@ -739,6 +750,7 @@ __device__ void read_ctl(const Ctl* c, Local& L) {
     sL.extra_s = __ldcg(&c->extra_s);
     sL.step_off_cur = __ldcg(&c->step_off_cur);
     sL.done = __ldcg(&c->done);
+    sL.s_int = __ldcg(&c->s_int);
   }
   __syncthreads();
   const uint32_t rid = L.rid, qsel = L.qsel;
@@ -776,7 +788,7 @@ __global__ void __launch_bounds__(kMaxBlock, 2) k_eic(KArgs A) {
   Ctl* c = A.ctl;
   uint32_t gen = __ldcg(&c->bar.gen);
   Local L;
-  L.rid = __ldcg(&c->round_base);
+  L.rid = 0;
   L.qsel = 0;
   read_ctl(c, L);
   L.cur_cnt = 1;  // the first round's frontier is {s}
@@ -792,7 +804,7 @@ __global__ void __launch_bounds__(kMaxBlock, 2) k_eic(KArgs A) {
     B.j0 = 1;
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) tl_mark(A, 0, L.rid);
-  bool alive = true;
+  bool alive = !L.done;  // an isolated source has nothing to relax
   uint32_t total_rounds = 0;
   constexpr uint32_t kMaxRounds = 1u << 22;  // every block counts the same rounds and stops together
   while (alive) {
@@ -812,7 +824,13 @@ __global__ void __launch_bounds__(kMaxBlock, 2) k_eic(KArgs A) {
         c->tcnt[(L.rid + 1) % 3] = 0;
         c->work[(L.rid + 1) % 3] = 0;
       }
+      {  // the other bitmap served round rid-1 and is next used in round rid+1: clear it now
+        uint32_t* other = A.fbits + ((L.rid + 1) & 1u) * A.fwords;
+        for (uint32_t wi = blockIdx.x * blockDim.x + threadIdx.x; wi < A.fwords; wi += gridDim.x * blockDim.x)
+          __stcg(&other[wi], 0u);
+      }
       RoundCtx R;
+      R.fbits = A.fbits + (L.rid & 1u) * A.fwords;
       R.lb = L.lb;
       R.ub = L.ub;
       R.ub_eff = L.ub < (int64_t)EIC_INF ? L.ub : (int64_t)EIC_INF;
@@ -895,7 +913,7 @@ __global__ void __launch_bounds__(kMaxBlock, 2) k_eic(KArgs A) {
           d = __ldcg(&A.dist[x]);
           take = true;
           if (step1 && d64(d) >= L.ub) {  // first step: keep only what is final
-            if (x != A.s) __stcg(&A.dist[x], EIC_INF);
+            if (x != L.s_int) __stcg(&A.dist[x], EIC_INF);
             take = false;
           }
         }
@@ -906,13 +924,14 @@ __global__ void __launch_bounds__(kMaxBlock, 2) k_eic(KArgs A) {
             __stcg(&A.sd[slot], d);
             __stcg(&A.scur[slot], kNone);  // the first step's windows used a larger ub
           }
-        } else if (take) {
-          __stcg(&A.sd[idx], d);
-          __stcg(&A.scur[idx], __ldcg(&A.cursor[x]));
         }
         if (take) {
           atomicOr(&A.sbits[x >> 5], 1u << (x & 31));
           const uint32_t dg = __ldg(&A.G.row[x + 1]) - __ldg(&A.G.row[x]);
+          if (!step1) {
+            __stcg(&A.sd[idx], d);
+            __stcg(&A.scur[idx], dg > kCursorMin ? __ldcg(&A.cursor[x]) : kNone);
+          }
           if (dg > 0) {  // degree-0 vertices (an isolated source) carry no rank
             const uint32_t r = __ldg(&A.G.drank[dg]);
             if (r < (uint32_t)kShRanks)
@@ -983,8 +1002,6 @@ __global__ void __launch_bounds__(kMaxBlock, 2) k_eic(KArgs A) {
     read_ctl(c, L);
     if (L.done) break;
   }
-  // the next query's stamp ids start above every id any block used
-  if (threadIdx.x == 0) atomicMax(&c->round_base, L.rid);
   if (blockIdx.x == 0 && threadIdx.x == 0 && A.status_out) *A.status_out = ld_volatile_int(&c->status);
 }
 
@@ -994,18 +1011,23 @@ __global__ void k_init(KArgs A) {
   for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < G.D; r += gridDim.x * blockDim.x) A.hist[r] = G.dcnt0[r];
   for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r <= A.ring_mask; r += gridDim.x * blockDim.x) A.ring[r] = 0;
   if (blockIdx.x == 0 && threadIdx.x == 0) {
-    A.dist[A.s] = 0;
-    A.q0[0] = A.s;
-    A.touched[0] = A.s;
+    const uint32_t si = G.orig2int[A.s];
+    c->s_int = si;
+    uint32_t dgs = 0;
+    if (si != EIC_INF) {
+      A.dist[si] = 0;
+      A.q0[0] = si;
+      A.touched[0] = si;
+      dgs = G.row[si + 1] - G.row[si];
+    }
     A.step_off[1] = 0;
     A.step_ub[0] = 0;
-    const uint32_t dgs = G.row[A.s + 1] - G.row[A.s];
     c->lb = 0;
     c->ub = EIC_INF_T;
     c->st = 0;
     c->lb0 = 0;
     c->step = 1;
-    c->done = 0;
+    c->done = si == EIC_INF ? 1u : 0u;
     c->push_beg = c->push_end = 0;
     c->pull_on = c->pull_cnt = c->extra_s = 0;
     c->step_off_cur = 0;
@@ -1035,20 +1057,34 @@ __global__ void k_init(KArgs A) {
   }
 }
 
-// parent[v] = smallest-id u with dist[u] + w(u, v) == dist[v]; one warp per vertex.
-__global__ void k_parent(DevGraph G, const uint32_t* __restrict__ dist, uint32_t s, uint32_t* parent) {
+// Distances in the caller's numbering: out[u] = dist[orig2int[u]], +inf for
+// isolated vertices, 0 for the source.
+__global__ void k_output(DevGraph G, const uint32_t* __restrict__ idist, uint32_t s, uint32_t* out) {
+  for (uint64_t u = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; u < G.n; u += (uint64_t)gridDim.x * blockDim.x) {
+    const uint32_t i = __ldg(&G.orig2int[u]);
+    out[u] = u == s ? 0u : (i == EIC_INF ? EIC_INF : __ldcg(&idist[i]));
+  }
+}
+
+// parent[v] = smallest original id u with dist[u] + w(u, v) == dist[v] (one
+// warp per vertex); parent[s] = s, +inf where unreachable.
+__global__ void k_parent(DevGraph G, const uint32_t* __restrict__ idist, uint32_t s, uint32_t* parent) {
   const uint32_t lane = lane_id();
   const uint64_t nw = (uint64_t)gridDim.x * (blockDim.x >> 5);
   for (uint64_t v = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); v < G.n; v += nw) {
-    const uint32_t dv = dist[v];
+    const uint32_t vi = G.orig2int[v];
+    const uint32_t dv = vi == EIC_INF ? EIC_INF : idist[vi];
     uint32_t best = EIC_INF;
     if (v != s && dv != EIC_INF) {
-      const uint32_t rb = G.row[v], re = G.row[v + 1];
+      const uint32_t rb = G.row[vi], re = G.row[vi + 1];
       for (uint32_t i = rb + lane; i < re; i += 32) {
         const uint2 ent = G.adj[i];
         if (ent.y > dv) break;
-        const uint32_t du = dist[ent.x];
-        if (du != EIC_INF && (uint64_t)du + ent.y == dv && ent.x < best) best = ent.x;
+        const uint32_t du = idist[ent.x];
+        if (du != EIC_INF && (uint64_t)du + ent.y == dv) {
+          const uint32_t uo = G.int2orig[ent.x];
+          best = uo < best ? uo : best;
+        }
       }
       for (int o = 16; o > 0; o >>= 1) best = min(best, __shfl_xor_sync(EIC_FULL_MASK, best, o));
     }
@@ -1130,8 +1166,10 @@ KArgs make_args(eic_graph* g, uint32_t s, uint32_t* dist, const eic_params& p, i
   Workspace& w = g->ws;
   KArgs A;
   A.G = g->dg;
-  A.dist = dist;
-  A.stamp = w.stamp;
+  A.dist = w.idist;
+  A.out = dist;
+  A.fbits = w.fbits;
+  A.fwords = (uint32_t)(g->dg.ni / 32 + 2);
   A.cursor = w.cursor;
   A.q0 = w.q[0];
   A.q1 = w.q[1];
@@ -1173,13 +1211,9 @@ int enqueue_query(eic_graph* g, uint32_t s, uint32_t* dist, uint32_t* parent, co
   const int block = p.block_threads ? (int)p.block_threads : kDefaultBlock;
   int rc = launch_shape(&w, block);
   if (rc) return rc;
-  if (w.host_round_base > (1u << 30)) {  // keep stamp ids far from wrapping
-    EIC_CUDA_TRY(cudaMemsetAsync(w.stamp, 0, (uint64_t)w.n * 4, st));
-    EIC_CUDA_TRY(cudaMemsetAsync(&w.ctl->round_base, 0, 4, st));
-    w.host_round_base = 0;
-  }
-  EIC_CUDA_TRY(cudaMemsetAsync(dist, 0xFF, (uint64_t)g->dg.n * 4, st));
-  EIC_CUDA_TRY(cudaMemsetAsync(w.sbits, 0, ((uint64_t)g->dg.n / 32 + 2) * 4, st));
+  EIC_CUDA_TRY(cudaMemsetAsync(w.idist, 0xFF, (uint64_t)g->dg.ni * 4, st));
+  EIC_CUDA_TRY(cudaMemsetAsync(w.sbits, 0, ((uint64_t)g->dg.ni / 32 + 2) * 4, st));
+  EIC_CUDA_TRY(cudaMemsetAsync(w.fbits, 0, 2 * ((uint64_t)g->dg.ni / 32 + 2) * 4, st));
   KArgs A = make_args(g, s, dist, p, status_out);
   if (timeline) {
     A.timeline = w.timeline;
@@ -1189,8 +1223,10 @@ int enqueue_query(eic_graph* g, uint32_t s, uint32_t* dist, uint32_t* parent, co
   EIC_CUDA_TRY(cudaGetLastError());
   void* args[] = {&A};
   EIC_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)k_eic, dim3(w.grid), dim3(block), args, 0, st));
+  k_output<<<2 * w.grid, 256, 0, st>>>(g->dg, w.idist, s, dist);
+  EIC_CUDA_TRY(cudaGetLastError());
   if (parent) {
-    k_parent<<<1024, 256, 0, st>>>(g->dg, dist, s, parent);
+    k_parent<<<1024, 256, 0, st>>>(g->dg, w.idist, s, parent);
     EIC_CUDA_TRY(cudaGetLastError());
   }
   return EIC_OK;
@@ -1211,7 +1247,8 @@ int trivial_query(eic_graph* g, uint32_t s, uint32_t* dist, uint32_t* parent, cu
 }  // namespace
 
 void eic_ws_free(Workspace* w) {
-  cudaFree(w->stamp);
+  cudaFree(w->idist);
+  cudaFree(w->fbits);
   cudaFree(w->q[0]);
   cudaFree(w->q[1]);
   cudaFree(w->sid);
@@ -1236,7 +1273,7 @@ int eic_ws_ensure(eic_graph* g, int) {
   Workspace* w = &g->ws;
   if (w->ctl) return EIC_OK;
   const DevGraph& G = g->dg;
-  const uint64_t n = G.n;
+  const uint64_t n = G.ni;  // per-vertex arrays cover the internal (non-isolated) vertices
   int rc = EIC_OK;
   uint32_t maxw = G.maxw ? G.maxw : 1;
   uint32_t bits = 0;
@@ -1247,8 +1284,8 @@ int eic_ws_ensure(eic_graph* g, int) {
   // and the windows of one round belong to distinct vertices
   w->task_cap = (uint32_t)(G.two_m / kHeavyMinFloor + 2);
   w->step_cap = kStepCap;
-  w->n = G.n;
-  if ((rc = walloc(w, &w->stamp, n)) || (rc = walloc(w, &w->q[0], n)) || (rc = walloc(w, &w->q[1], n)) ||
+  w->n = G.ni;
+  if ((rc = walloc(w, &w->idist, n)) || (rc = walloc(w, &w->fbits, 2 * (n / 32 + 2))) || (rc = walloc(w, &w->q[0], n)) || (rc = walloc(w, &w->q[1], n)) ||
       (rc = walloc(w, &w->sid, n + 2)) || (rc = walloc(w, &w->sd, n + 2)) ||
       (rc = walloc(w, &w->scur, n + 2)) || (rc = walloc(w, &w->cursor, n)) || (rc = walloc(w, &w->touched, n + 1)) || (rc = walloc(w, &w->sbits, n / 32 + 2)) ||
       (rc = walloc(w, &w->hist, (uint64_t)G.D + 1)) || (rc = walloc(w, &w->ring, 1ull << w->ring_bits)) ||
@@ -1263,7 +1300,7 @@ int eic_ws_ensure(eic_graph* g, int) {
     eic_ws_free(w);
     return EIC_ENOMEM;
   }
-  if (cudaMemset(w->stamp, 0, n * 4) != cudaSuccess || cudaMemset(w->ctl, 0, sizeof(Ctl)) != cudaSuccess) {
+  if (cudaMemset(w->ctl, 0, sizeof(Ctl)) != cudaSuccess) {
     (void)cudaGetLastError();
     eic_ws_free(w);
     return EIC_ECUDA;
@@ -1318,7 +1355,6 @@ int eic_sssp(const eic_graph* gc, uint32_t source, uint32_t* dist, uint32_t* par
   EIC_CUDA_TRY(cudaMemcpyAsync(w.ctl_host, w.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
   EIC_CUDA_TRY(cudaStreamSynchronize(st));
   const Ctl& h = *w.ctl_host;
-  w.host_round_base = h.round_base;
   if (stats) {
     stats->steps = h.trace_len;
     stats->rounds = h.cnt_rounds;
@@ -1404,14 +1440,6 @@ int eic_sssp_batch(const eic_graph* const* graphs, const uint32_t* sources, uint
     if (statuses) statuses[i] = s_i;
     if (first_err == EIC_OK && s_i != EIC_OK) first_err = s_i;
   }
-  for (uint32_t i = 0; i < num_queries; ++i) {  // refresh stamp-id bases
-    eic_graph* g = const_cast<eic_graph*>(graphs[i]);
-    if (g->ws.ctl && g->ws.ctl_host) {
-      DeviceGuard dg(g->device);
-      if (cudaMemcpy(&g->ws.host_round_base, &g->ws.ctl->round_base, 4, cudaMemcpyDeviceToHost) != cudaSuccess)
-        (void)cudaGetLastError();
-    }
-  }
   return first_err;
 }
 
@@ -1433,8 +1461,9 @@ constexpr uint32_t kNaRingBits = 16;  // 2^16 > EIC_NOALLOC_MAX_WEIGHT
 constexpr uint64_t kNaTasks = kNaE / kHeavyMinFloor + 2;
 
 constexpr uint64_t na_align(uint64_t x) { return (x + 255) & ~255ull; }
-constexpr uint64_t kNaStamp = 0;
-constexpr uint64_t kNaCursor = kNaStamp + na_align(kNaN * 4);
+constexpr uint64_t kNaIdist = 0;
+constexpr uint64_t kNaFbits = kNaIdist + na_align(kNaN * 4);
+constexpr uint64_t kNaCursor = kNaFbits + na_align(2 * (kNaN / 32 + 2) * 4);
 constexpr uint64_t kNaQ0 = kNaCursor + na_align(kNaN * 4);
 constexpr uint64_t kNaQ1 = kNaQ0 + na_align(kNaN * 4);
 constexpr uint64_t kNaSid = kNaQ1 + na_align(kNaN * 4);
@@ -1456,14 +1485,13 @@ struct NaDevice {
   bool ready = false;
   unsigned char* base = nullptr;  // device address of g_na_scratch on this device
   int grid = 0;
-  uint32_t round_base = 0;
 };
 NaDevice g_na[kMaxDevices];
 std::mutex g_na_mu;
 
 // Once per device, with that device current: the scratch's device address
-// (the symbol's host-side name is not a device pointer), cleared stamps and
-// control block, and the cooperative grid shape.
+// (the symbol's host-side name is not a device pointer), a cleared control
+// block, and the cooperative grid shape.
 int na_setup(NaDevice& d, cudaStream_t st) {
   void* ptr = nullptr;
   EIC_CUDA_TRY(cudaGetSymbolAddress(&ptr, g_na_scratch));
@@ -1476,12 +1504,10 @@ int na_setup(NaDevice& d, cudaStream_t st) {
   EIC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_eic, kDefaultBlock, 0));
   if (per_sm < 1) return EIC_ECUDA;
   unsigned char* base = (unsigned char*)ptr;
-  EIC_CUDA_TRY(cudaMemsetAsync(base + kNaStamp, 0, kNaN * 4, st));
   EIC_CUDA_TRY(cudaMemsetAsync(base + kNaCtl, 0, sizeof(Ctl), st));
   EIC_CUDA_TRY(cudaStreamSynchronize(st));
   d.base = base;
   d.grid = sms * per_sm;
-  d.round_base = 0;
   d.ready = true;
   return EIC_OK;
 }
@@ -1508,14 +1534,12 @@ extern "C" int eic_sssp_noalloc(const eic_graph* gc, uint32_t source, uint32_t* 
   }
   unsigned char* b = nd.base;
   Ctl* ctl = (Ctl*)(b + kNaCtl);
-  if (nd.round_base > (1u << 30)) {  // keep stamp ids far from wrapping
-    EIC_CUDA_TRY(cudaMemsetAsync(b + kNaStamp, 0, kNaN * 4, st));
-    EIC_CUDA_TRY(cudaMemsetAsync(&ctl->round_base, 0, 4, st));
-  }
   KArgs A;
   A.G = G;
-  A.dist = dist;
-  A.stamp = (uint32_t*)(b + kNaStamp);
+  A.dist = (uint32_t*)(b + kNaIdist);
+  A.out = dist;
+  A.fbits = (uint32_t*)(b + kNaFbits);
+  A.fwords = (uint32_t)(G.ni / 32 + 2);
   A.cursor = (uint32_t*)(b + kNaCursor);
   A.q0 = (uint32_t*)(b + kNaQ0);
   A.q1 = (uint32_t*)(b + kNaQ1);
@@ -1547,19 +1571,17 @@ extern "C" int eic_sssp_noalloc(const eic_graph* gc, uint32_t source, uint32_t* 
   A.trace_cap = 0;
   A.timeline = nullptr;
   A.timeline_cap = 0;
-  EIC_CUDA_TRY(cudaMemsetAsync(dist, 0xFF, (uint64_t)G.n * 4, st));
-  EIC_CUDA_TRY(cudaMemsetAsync(A.sbits, 0, ((uint64_t)G.n / 32 + 2) * 4, st));
+  EIC_CUDA_TRY(cudaMemsetAsync(A.dist, 0xFF, (uint64_t)G.ni * 4, st));
+  EIC_CUDA_TRY(cudaMemsetAsync(A.sbits, 0, ((uint64_t)G.ni / 32 + 2) * 4, st));
+  EIC_CUDA_TRY(cudaMemsetAsync(A.fbits, 0, 2 * ((uint64_t)G.ni / 32 + 2) * 4, st));
   k_init<<<64, 256, 0, st>>>(A);
   EIC_CUDA_TRY(cudaGetLastError());
   void* args[] = {&A};
   EIC_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)k_eic, dim3(nd.grid), dim3(kDefaultBlock), args, 0, st));
-  struct {
-    int status;
-    uint32_t round_base;
-  } h = {0, 0};
-  EIC_CUDA_TRY(cudaMemcpyAsync(&h.status, &ctl->status, sizeof(int), cudaMemcpyDeviceToHost, st));
-  EIC_CUDA_TRY(cudaMemcpyAsync(&h.round_base, &ctl->round_base, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+  k_output<<<2 * nd.grid, 256, 0, st>>>(G, A.dist, source, dist);
+  EIC_CUDA_TRY(cudaGetLastError());
+  int status = 0;
+  EIC_CUDA_TRY(cudaMemcpyAsync(&status, &ctl->status, sizeof(int), cudaMemcpyDeviceToHost, st));
   EIC_CUDA_TRY(cudaStreamSynchronize(st));
-  nd.round_base = h.round_base;
-  return h.status;
+  return status;
 }
