@@ -37,7 +37,7 @@ struct DevGraph {
   const uint32_t* dcnt0;  // [D] number of vertices with degree dvals[r]
   uint32_t D;
   const uint32_t* rtow;   // [EIC_RATIO_NUM] maxW(G, i / (RATIO_NUM - 1))
-  const uint2* nz;        // [nz_count = ni] {internal id, smallest row weight}, by (weight, id)
+  const uint4* nz;        // [nz_count = ni] {internal id, smallest row weight, row begin, row end}, by (weight, id)
   uint32_t nz_count;
   const uint32_t* nz_lt;  // [nz_lt_len] nz_lt[t] = number of nz entries with smallest weight < t
   uint32_t nz_lt_len;

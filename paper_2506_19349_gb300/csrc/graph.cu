@@ -144,10 +144,10 @@ __global__ void k_gather_u32(const uint32_t* __restrict__ src, const uint32_t* _
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += gridDim.x * blockDim.x) out[i] = src[idx[i]];
 }
 
-// nz[i] = {i, smallest weight of row i} for every internal vertex
-__global__ void k_nz_fill(const uint32_t* __restrict__ row, const uint2* __restrict__ adj, uint32_t ni, uint2* nz) {
+// nz[i] = {i, smallest weight of row i, row begin, row end} for every internal vertex
+__global__ void k_nz_fill(const uint32_t* __restrict__ row, const uint2* __restrict__ adj, uint32_t ni, uint4* nz) {
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < ni; i += gridDim.x * blockDim.x)
-    nz[i] = make_uint2(i, adj[row[i]].y);
+    nz[i] = make_uint4(i, adj[row[i]].y, row[i], row[i + 1]);
 }
 
 __global__ void k_pack_adj(const uint64_t* __restrict__ keys, const uint32_t* __restrict__ vals, uint64_t E,
@@ -226,19 +226,22 @@ __global__ void k_narrow(const uint64_t* __restrict__ in, uint64_t n, uint32_t* 
     out[i] = (uint32_t)in[i];
 }
 
-__global__ void k_nz_keys(const uint2* __restrict__ nz, uint32_t cnt, int vbits, uint64_t* keys) {
+__global__ void k_nz_keys(const uint4* __restrict__ nz, uint32_t cnt, int vbits, uint64_t* keys) {
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += gridDim.x * blockDim.x)
     keys[i] = ((uint64_t)nz[i].y << vbits) | nz[i].x;
 }
 
-__global__ void k_nz_from_keys(const uint64_t* __restrict__ keys, uint32_t cnt, int vbits, uint2* nz) {
+__global__ void k_nz_from_keys(const uint64_t* __restrict__ keys, uint32_t cnt, int vbits,
+                               const uint32_t* __restrict__ row, uint4* nz) {
   const uint64_t vmask = (1ull << vbits) - 1;
-  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += gridDim.x * blockDim.x)
-    nz[i] = make_uint2((uint32_t)(keys[i] & vmask), (uint32_t)(keys[i] >> vbits));
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += gridDim.x * blockDim.x) {
+    const uint32_t v = (uint32_t)(keys[i] & vmask);
+    nz[i] = make_uint4(v, (uint32_t)(keys[i] >> vbits), row[v], row[v + 1]);
+  }
 }
 
 // lt[t] = number of entries of the weight-sorted nz with smallest weight < t, t < len
-__global__ void k_nz_lt(const uint2* __restrict__ nz, uint32_t cnt, uint32_t len, uint32_t* lt) {
+__global__ void k_nz_lt(const uint4* __restrict__ nz, uint32_t cnt, uint32_t len, uint32_t* lt) {
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i <= cnt; i += gridDim.x * blockDim.x) {
     const uint32_t lo = i == 0 ? 0 : nz[i - 1].y + 1;           // first t with entry i-1 counted
     const uint32_t hi = i == cnt ? len - 1 : nz[i].y;           // last t before entry i counts
@@ -536,7 +539,7 @@ int build(eic_graph* g, const uint32_t* src, const uint32_t* dst, const uint32_t
       k_nz_keys<<<grid_for(ni), kThreads, 0, st>>>(g->nz, ni, ibits, kk0);
       bool alt = false;
       TRY(radix_sort(kk0, nullptr, kk1, nullptr, ni, ibits + wbits, hist_scratch, st, &alt));
-      k_nz_from_keys<<<grid_for(ni), kThreads, 0, st>>>(alt ? kk1 : kk0, ni, ibits, g->nz);
+      k_nz_from_keys<<<grid_for(ni), kThreads, 0, st>>>(alt ? kk1 : kk0, ni, ibits, g->row, g->nz);
       EIC_CUDA_TRY(cudaGetLastError());
       EIC_CUDA_TRY(cudaStreamSynchronize(st));
       tmp.release(kk0);

@@ -54,6 +54,7 @@ struct Workspace {
   uint32_t* sid = nullptr;   // settled list: vertex
   uint32_t* sd = nullptr;    // settled list: final distance
   uint32_t* scur = nullptr;  // settled list: window cursor (offset in the row)
+  uint2* srow = nullptr;     // settled list: row begin, row end
   uint32_t* cursor = nullptr;
   uint32_t* touched = nullptr;
   uint32_t* sbits = nullptr;  // settled bitmap
@@ -81,7 +82,7 @@ struct eic_graph {
   uint32_t* dvals = nullptr;
   uint32_t* dcnt0 = nullptr;
   uint32_t* rtow = nullptr;
-  uint2* nz = nullptr;
+  uint4* nz = nullptr;
   uint32_t* nz_lt = nullptr;
   uint32_t* orig2int = nullptr;
   uint32_t* int2orig = nullptr;

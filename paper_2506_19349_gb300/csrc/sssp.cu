@@ -58,6 +58,7 @@ struct KArgs {
   uint32_t* sid;
   uint32_t* sd;
   uint32_t* scur;
+  uint2* srow;
   uint32_t* touched;
   uint32_t* sbits;  // settled bitmap
   uint32_t* hist;
@@ -348,13 +349,13 @@ __device__ void round_phase(const KArgs& A, const RoundCtx& R, const Local& L, R
             len = e - b;
           }
         }
-      } else if (i < np) {  // push set: settled, lb0 <= dist <= st
+      } else if (i < np) {  // push set: settled, lb0 <= dist <= st (all from the settled list)
         const uint32_t idx = L.push_beg + i;
-        u = __ldcg(&A.sid[idx]);
         const uint32_t d = __ldcg(&A.sd[idx]);
         val = d;
         if ((int64_t)d >= R.lb0 && (int64_t)d <= R.st) {
-          const uint32_t rb = __ldg(&A.G.row[u]), re = __ldg(&A.G.row[u + 1]);
+          const uint2 rr = __ldcg(&A.srow[idx]);
+          const uint32_t rb = rr.x, re = rr.y;
           if (!(d > 0 && re - rb == 1)) {
             C.frontier += 1;
             const uint32_t cur = __ldcg(&A.scur[idx]);
@@ -367,14 +368,15 @@ __device__ void round_phase(const KArgs& A, const RoundCtx& R, const Local& L, R
           }
         }
       } else {  // pull set: unsettled, smallest weight < ub - st (Function 1)
-        u = __ldg(&A.G.nz[i - np].x);
+        const uint4 z = __ldg(&A.G.nz[i - np]);
+        u = z.x;
         mode = kModePull;
         const uint32_t bits = __ldcg(&A.sbits[u >> 5]);
         if (!((bits >> (u & 31)) & 1u)) {
           C.pitems += 1;
           // the row's first weight is below the bound (nz order): gallop from the second
-          b = __ldg(&A.G.row[u]);
-          len = gallop_w(A.G.adj, b + 1, __ldg(&A.G.row[u + 1]), pull_bound) - b;
+          b = z.z;
+          len = gallop_w(A.G.adj, b + 1, z.w, pull_bound) - b;
         }
       }
     }
@@ -664,6 +666,7 @@ __device__ void step_boundary(const KArgs& A, PhaseScr& P, BState& B, const Loca
       A.sid[scnt] = L.s_int;
       A.sd[scnt] = 0;
       A.scur[scnt] = kNone;
+      A.srow[scnt] = make_uint2(G.row[L.s_int], G.row[L.s_int + 1]);
       ++scnt;
       extra = 1;
     }
@@ -907,10 +910,12 @@ __global__ void __launch_bounds__(kMaxBlock, 2) k_eic(KArgs A) {
       for (uint32_t base = lbeg + blockIdx.x * blockDim.x; base < lend; base += nthreads) {
         const uint32_t idx = base + threadIdx.x;
         bool take = false;
-        uint32_t x = 0, d = 0;
+        uint32_t x = 0, d = 0, xrb = 0, xre = 0;
         if (idx < lend) {
           x = __ldcg(&list[idx]);
           d = __ldcg(&A.dist[x]);
+          xrb = __ldg(&A.G.row[x]);
+          xre = __ldg(&A.G.row[x + 1]);
           take = true;
           if (step1 && d64(d) >= L.ub) {  // first step: keep only what is final
             if (x != L.s_int) __stcg(&A.dist[x], EIC_INF);
@@ -923,14 +928,16 @@ __global__ void __launch_bounds__(kMaxBlock, 2) k_eic(KArgs A) {
             __stcg(&A.sid[slot], x);
             __stcg(&A.sd[slot], d);
             __stcg(&A.scur[slot], kNone);  // the first step's windows used a larger ub
+            __stcg(&A.srow[slot], make_uint2(xrb, xre));
           }
         }
         if (take) {
           atomicOr(&A.sbits[x >> 5], 1u << (x & 31));
-          const uint32_t dg = __ldg(&A.G.row[x + 1]) - __ldg(&A.G.row[x]);
+          const uint32_t dg = xre - xrb;
           if (!step1) {
             __stcg(&A.sd[idx], d);
             __stcg(&A.scur[idx], dg > kCursorMin ? __ldcg(&A.cursor[x]) : kNone);
+            __stcg(&A.srow[idx], make_uint2(xrb, xre));
           }
           if (dg > 0) {  // degree-0 vertices (an isolated source) carry no rank
             const uint32_t r = __ldg(&A.G.drank[dg]);
@@ -1176,6 +1183,7 @@ KArgs make_args(eic_graph* g, uint32_t s, uint32_t* dist, const eic_params& p, i
   A.sid = w.sid;
   A.sd = w.sd;
   A.scur = w.scur;
+  A.srow = w.srow;
   A.touched = w.touched;
   A.sbits = w.sbits;
   A.hist = w.hist;
@@ -1254,6 +1262,7 @@ void eic_ws_free(Workspace* w) {
   cudaFree(w->sid);
   cudaFree(w->sd);
   cudaFree(w->scur);
+  cudaFree(w->srow);
   cudaFree(w->cursor);
   cudaFree(w->touched);
   cudaFree(w->sbits);
@@ -1287,7 +1296,7 @@ int eic_ws_ensure(eic_graph* g, int) {
   w->n = G.ni;
   if ((rc = walloc(w, &w->idist, n)) || (rc = walloc(w, &w->fbits, 2 * (n / 32 + 2))) || (rc = walloc(w, &w->q[0], n)) || (rc = walloc(w, &w->q[1], n)) ||
       (rc = walloc(w, &w->sid, n + 2)) || (rc = walloc(w, &w->sd, n + 2)) ||
-      (rc = walloc(w, &w->scur, n + 2)) || (rc = walloc(w, &w->cursor, n)) || (rc = walloc(w, &w->touched, n + 1)) || (rc = walloc(w, &w->sbits, n / 32 + 2)) ||
+      (rc = walloc(w, &w->scur, n + 2)) || (rc = walloc(w, &w->srow, n + 2)) || (rc = walloc(w, &w->cursor, n)) || (rc = walloc(w, &w->touched, n + 1)) || (rc = walloc(w, &w->sbits, n / 32 + 2)) ||
       (rc = walloc(w, &w->hist, (uint64_t)G.D + 1)) || (rc = walloc(w, &w->ring, 1ull << w->ring_bits)) ||
       (rc = walloc(w, &w->tasks, w->task_cap)) || (rc = walloc(w, &w->step_ub, (uint64_t)kStepCap + 2)) ||
       (rc = walloc(w, &w->step_off, (uint64_t)kStepCap + 2)) || (rc = walloc(w, &w->trace, kTraceCap)) || (rc = walloc(w, &w->timeline, 2ull * kTimelineCap)) ||
@@ -1469,7 +1478,8 @@ constexpr uint64_t kNaQ1 = kNaQ0 + na_align(kNaN * 4);
 constexpr uint64_t kNaSid = kNaQ1 + na_align(kNaN * 4);
 constexpr uint64_t kNaSd = kNaSid + na_align((kNaN + 2) * 4);
 constexpr uint64_t kNaScur = kNaSd + na_align((kNaN + 2) * 4);
-constexpr uint64_t kNaTouched = kNaScur + na_align((kNaN + 2) * 4);
+constexpr uint64_t kNaSrow = kNaScur + na_align((kNaN + 2) * 4);
+constexpr uint64_t kNaTouched = kNaSrow + na_align((kNaN + 2) * 8);
 constexpr uint64_t kNaSbits = kNaTouched + na_align((kNaN + 1) * 4);
 constexpr uint64_t kNaHist = kNaSbits + na_align((kNaN / 32 + 2) * 4);
 constexpr uint64_t kNaRing = kNaHist + na_align(kNaD * 4);
@@ -1546,6 +1556,7 @@ extern "C" int eic_sssp_noalloc(const eic_graph* gc, uint32_t source, uint32_t* 
   A.sid = (uint32_t*)(b + kNaSid);
   A.sd = (uint32_t*)(b + kNaSd);
   A.scur = (uint32_t*)(b + kNaScur);
+  A.srow = (uint2*)(b + kNaSrow);
   A.touched = (uint32_t*)(b + kNaTouched);
   A.sbits = (uint32_t*)(b + kNaSbits);
   A.hist = (uint32_t*)(b + kNaHist);
