@@ -52,6 +52,7 @@ def parse_args():
     ap.add_argument("--cpu-sample", type=int, default=1, help="oracle queries timed for cpu_baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched measurements")
     return ap.parse_args()
 
 
@@ -60,6 +61,24 @@ def dist_env():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", str(rank)))
     return rank, world, local
+
+
+# DRAM bytes (read + write) of one query-kernel launch on the default workload,
+# from an ncu capture (profiles/k_eic_kron25_launches.md), valid only for the
+# kernel sources it was taken on; any change to them reports null.
+KERNEL_SOURCES = ("paper_2506_19349_gb300/csrc/sssp.cu", "paper_2506_19349_gb300/csrc/common.cuh",
+                  "paper_2506_19349_gb300/csrc/graph.h", "paper_2506_19349_gb300/csrc/stats.cuh", "include/eic.h")
+MEASURED_TRAFFIC = {}  # {(scale, sources sha256): bytes per launch}
+
+
+def kernel_sources_sha256():
+    import hashlib
+
+    h = hashlib.sha256()
+    for rel in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
 
 
 def peaks():
@@ -185,6 +204,122 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def _degrees(eic, g, torch):
+    import numpy as np
+
+    rowp = np.empty(g.n + 1, dtype=np.uint64)
+    eic.load_library().eic_graph_export(g.handle, rowp.ctypes.data, None, None, None)
+    return torch.from_numpy(np.diff(rowp).astype(np.int64)).cuda()
+
+
+def _m_c(deg, d):
+    return int(deg[d != -1].sum().item() // 2)
+
+
+def batch_run_timed(b, stream, torch, runs):
+    """Device time (ms) of each of `runs` whole-batch runs of a prepared batch."""
+    out = []
+    for _ in range(runs):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        b.run(stream)
+        e1.record(stream)
+        st = b.wait(stream)
+        if (st != 0).any():
+            raise RuntimeError(f"batch statuses {sorted(set(st.tolist()))}")
+        out.append(e0.elapsed_time(e1))
+    return out
+
+
+def batched_same_workload(eic, torch, g, srcs, dists, stream, runs, plain_gteps, edges):
+    """The same queries as one tuned persistent batch (eic_batch_*)."""
+    import numpy as np
+
+    ref = [eic.to_host_u32(d).copy() for d in dists]
+    b = eic.Batch([g] * len(srcs), srcs, dists)
+    t0 = time.perf_counter()
+    cfg = b.tune(stream)
+    tune_s = time.perf_counter() - t0
+    batch_run_timed(b, stream, torch, 1)  # first run captures the CUDA graph
+    ms = batch_run_timed(b, stream, torch, runs)
+    same = all(np.array_equal(eic.to_host_u32(d), r) for d, r in zip(dists, ref))
+    info = b.info()
+    b.close()
+    gteps = edges / (statistics.mean(ms) * 1e-3) / 1e9
+    return {"value": gteps, "unit": "GTEPS", "ms_per_batch": statistics.mean(ms), "runs": runs,
+            "speedup_vs_plain": gteps / plain_gteps, "identical_to_plain": same, "tune_s": tune_s,
+            "config": {k: info[k] for k in ("groups", "blocks_per_group", "block_threads", "cuda_graph", "gap_shift",
+                                            "heavy_min", "scratch_bytes")},
+            "gpu_launches_per_batch": 2}
+
+
+def batched_mixed(eic, torch, stream, runs):
+    """32 graphs of uneven size x 8 sources: one tuned persistent batch vs 256
+    sequential plain calls (the plain path's per-query latency is reported too)."""
+    import numpy as np
+    from paper_2506_19349_gb300 import graphgen
+
+    t0 = time.perf_counter()
+    wls = graphgen.batch_set()
+    gen_s = time.perf_counter() - t0
+    graphs, srcs, degs = [], [], []
+    for wl in wls:
+        g = eic.Graph(wl.n, wl.src, wl.dst, wl.w)
+        deg = _degrees(eic, g, torch)
+        for s in wl.sources:
+            graphs.append(g)
+            srcs.append(int(s))
+            degs.append(deg)
+    del wls
+    dists = [eic.new_dist(g.n) for g in graphs]
+
+    def plain_pass():
+        evs = []
+        for g, s, d in zip(graphs, srcs, dists):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            eic.sssp(g, s, dist=d)
+            e1.record(stream)
+            evs.append((e0, e1))
+        torch.cuda.synchronize()
+        return [a.elapsed_time(b) for a, b in evs]
+
+    plain_pass()  # warm-up
+    edges = sum(_m_c(deg, d) for deg, d in zip(degs, dists))
+    ref = [eic.to_host_u32(d).copy() for d in dists]
+    p0 = torch.cuda.Event(enable_timing=True)
+    p1 = torch.cuda.Event(enable_timing=True)
+    p0.record(stream)
+    lat = plain_pass()
+    p1.record(stream)
+    torch.cuda.synchronize()
+    plain_ms = p0.elapsed_time(p1)
+    b = eic.Batch(graphs, srcs, dists)
+    t0 = time.perf_counter()
+    cfg = b.tune(stream)
+    tune_s = time.perf_counter() - t0
+    batch_run_timed(b, stream, torch, 1)  # first run captures the CUDA graph
+    ms = batch_run_timed(b, stream, torch, runs)
+    same = all(np.array_equal(eic.to_host_u32(d), r) for d, r in zip(dists, ref))
+    info = b.info()
+    b.close()
+    lat.sort()
+    plain_gteps = edges / (plain_ms * 1e-3) / 1e9
+    gteps = edges / (statistics.mean(ms) * 1e-3) / 1e9
+    return {"workload": "32 graphs: RMAT scales 12..22 (two seeds each) and grids 256^2 x3, 512^2 x3, 1024^2 x2, "
+                        "2048^2 x2 (10% edges deleted, 2% diagonals), weights uniform [1,255], 8 sources each",
+            "queries": len(srcs), "generate_s": gen_s,
+            "plain": {"value": plain_gteps, "unit": "GTEPS", "ms": plain_ms,
+                      "latency_ms": {"p50": lat[len(lat) // 2], "p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))]}},
+            "batched": {"value": gteps, "unit": "GTEPS", "ms_per_batch": statistics.mean(ms), "runs": runs,
+                        "tune_s": tune_s, "identical_to_plain": same,
+                        "config": {k: info[k] for k in ("groups", "blocks_per_group", "block_threads", "cuda_graph",
+                                                        "gap_shift", "heavy_min", "scratch_bytes")}},
+            "speedup": gteps / plain_gteps}
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
@@ -217,6 +352,7 @@ def main():
     torch.cuda.synchronize()
     build_s = time.perf_counter() - t0
     n = g.n
+    m_edges = g.m
     srcs = [int(s) for s in wl.sources]
     q = len(srcs)
     dists = [eic.new_dist(n) for _ in range(q)]
@@ -280,7 +416,8 @@ def main():
     # roofline of the query kernel: algorithmic bytes per launch over its event duration
     b_alg = [16 * inf["frontier"] + 12 * inf["traversed"] + 8 * inf["improved"] + 12 * inf["pull_items"] + 4 * n
              for inf in all_infos]
-    achieved = statistics.mean(b / (t * 1e-3) / 1e9 for b, t in zip(b_alg, q_ms))
+    k_ms = [inf["kernel_ms"] for inf in all_infos]
+    achieved = statistics.mean(b / (t * 1e-3) / 1e9 for b, t in zip(b_alg, k_ms))
     peak, peak_kind = peaks()
 
     # ---- end to end: sources from pinned host memory, distances back to pinned host memory
@@ -311,6 +448,14 @@ def main():
         e2e = {"value": world * edges_per_step * args.steps / (e2e_ms * 1e-3) / 1e9, "unit": "GTEPS",
                "h2d_bytes_per_step": 4 * q, "d2h_bytes_per_step": 4 * n * q}
 
+    batched = None
+    if not args.no_batched:
+        batched = {"same_workload": batched_same_workload(eic, torch, g, srcs, dists, stream, max(args.steps, 1),
+                                                          value / world, edges_per_step)}
+        del g, dists, deg
+        torch.cuda.empty_cache()
+        batched["mixed_32_graphs"] = batched_mixed(eic, torch, stream, max(args.steps, 1))
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         _, cpu_gteps, cpu_t = oracle_baseline(wl, args.cpu_sample, oracle_m_c)
@@ -325,18 +470,22 @@ def main():
             "metric": METRIC, "value": value, "unit": "GTEPS", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-            "config": workload_config(wl, args.scale, q) | {"m": int(g.m), "m_c_mean": statistics.mean(m_c),
+            "config": workload_config(wl, args.scale, q) | {"m": int(m_edges), "m_c_mean": statistics.mean(m_c),
                                                             "build_s": build_s, "generate_s": gen_s},
             "latency_ms": {"p50": q_sorted[len(q_sorted) // 2], "p99": q_sorted[min(len(q_sorted) - 1,
                                                                                       int(0.99 * len(q_sorted)))],
                            "mean": statistics.mean(q_ms)},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
-                         "kernel": "k_eic (one launch per query, duration includes its dist/bitmap memsets)"},
-            "cpu_baseline": cpu, "clocks": clocks, "e2e": e2e, "gpu_launches": 2 * q * args.steps,
+                         "frac": achieved / peak,
+                         "traffic": MEASURED_TRAFFIC.get((args.scale, kernel_sources_sha256())),
+                         "peak_kind": peak_kind,
+                         "kernel": "k_eic (one launch per query; CUDA events around its launch)",
+                         "kernel_ms_mean": statistics.mean(k_ms), "alg_bytes_mean": statistics.mean(b_alg)},
+            "cpu_baseline": cpu, "clocks": clocks, "e2e": e2e, "gpu_launches": 3 * q * args.steps,
             "counters_mean": {k: statistics.mean(inf[k] for inf in all_infos)
                               for k in ("steps", "rounds", "frontier", "traversed", "pulls", "improved", "heavy",
                                         "pull_items")},
+            "batched": batched,
         }
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -35,6 +35,7 @@ extern "C" {
 #define EIC_ETIMEOUT 5  /* a bounded device-side wait (grid barrier) ran out; the context stays usable */
 #define EIC_EBUSY 6     /* the object is in use by another call */
 #define EIC_ESIZE 7     /* the graph exceeds the fixed limits of eic_sssp_noalloc */
+#define EIC_EABORT 8    /* batch: not run to the end, every block group stopped at an earlier error */
 
 /* Opaque, device-resident graph owned by the library (create/destroy). */
 typedef struct eic_graph eic_graph;
@@ -54,7 +55,11 @@ typedef struct eic_graph eic_graph;
  *   max_spin_log2 bound on each grid-barrier wait, 2^max_spin_log2 polls of
  *                 about 100 ns (0 = library choice, about 2 s); exceeding it
  *                 returns EIC_ETIMEOUT.
- *   flags         EIC_FLAG_* bits. */
+ *   flags         EIC_FLAG_* bits.
+ *   batch_groups  batches only: number of block groups that run queries at
+ *                 the same time (0 = library choice from the graph sizes;
+ *                 capped by the number of queries, the co-resident blocks and
+ *                 free device memory). */
 typedef struct {
   uint32_t alpha;
   double beta;
@@ -64,7 +69,8 @@ typedef struct {
   uint32_t heavy_min;
   uint32_t max_spin_log2;
   uint32_t flags;
-  uint32_t reserved[8];
+  uint32_t batch_groups;
+  uint32_t reserved[7];
 } eic_params;
 
 #define EIC_FLAG_NO_PULL 1u /* force st = lb (disable traversal optimisation; still exact) */
@@ -104,6 +110,10 @@ typedef struct {
   uint64_t* timeline;
   uint64_t timeline_cap;
   uint64_t timeline_len;
+  /* Device time of the query kernel alone (the persistent relaxation launch,
+   * without the setup memsets and the output pass), from CUDA events recorded
+   * around its launch on the call's stream. */
+  double kernel_ms;
 } eic_stats;
 
 /* Fill *p with the paper's defaults (Section 4.1). Returns EIC_EINVAL if p is NULL. */
@@ -176,15 +186,87 @@ int eic_sssp(const eic_graph* g, uint32_t source, uint32_t* dist, uint32_t* pare
 
 /*
  * num_queries queries (graphs[i], sources[i]) -> dists[i], with the same
- * semantics as eic_sssp. graphs and sources are host arrays; dists is a host
- * array of device pointers, one n_i-element uint32 buffer per query.
- * statuses (host array of num_queries ints, or NULL) receives each query's
- * status; the return value is the first non-OK status, or EIC_OK.
- * The queries are enqueued back to back on stream without host round trips;
- * the call synchronises once at the end.
+ * results as eic_sssp, in one cooperative persistent launch. The paper runs
+ * its trials one after another; this entry point adds query-level
+ * parallelism for many sources and many graphs of uneven size. The grid is
+ * cut into params->batch_groups groups of blocks (0 = library choice); each
+ * group claims the next query from a device work queue (largest graphs
+ * first), runs Algorithm 1 for it with its own scratch and a barrier over its
+ * own blocks, writes dists[i] and claims again.
+ *   graphs, sources   host arrays of num_queries; every graph on the current
+ *                     device. A graph may appear many times.
+ *   dists             host array of device pointers, one n_i-element uint32
+ *                     buffer per query, caller-owned; must not overlap.
+ *   statuses          host array of num_queries ints, or NULL; receives each
+ *                     query's status.
+ * The call reuses a per-device scratch pool (about 40 bytes per vertex plus
+ * one byte per adjacency entry of the largest graph, per group; grown when a
+ * batch needs more), launches on stream and synchronises it before
+ * returning. Returns the first non-OK status in query order, or EIC_OK.
+ * A group stops at its first failing query (that query reports the error);
+ * the other groups go on with the remaining queries. A query that no group
+ * finished reports EIC_EABORT.
+ * Errors: EIC_EINVAL, EIC_ENOMEM, EIC_ECUDA, and per query those of eic_sssp.
  */
 int eic_sssp_batch(const eic_graph* const* graphs, const uint32_t* sources, uint32_t num_queries,
                    uint32_t* const* dists, const eic_params* params, int* statuses, void* stream);
+
+/*
+ * A prepared batch for repeated runs (the batched form of eic_sssp_batch,
+ * replayed as a CUDA graph). It holds its own scratch, query table and
+ * status buffers; graphs and dists must stay valid until it is destroyed.
+ *
+ * eic_batch_create  validates and stores the queries (arguments as in
+ *                   eic_sssp_batch), allocates the scratch for the group
+ *                   count of params->batch_groups (0 = library choice).
+ *                   Synchronous. Errors: EIC_EINVAL, EIC_ENOMEM, EIC_ECUDA.
+ * eic_batch_run     enqueues one run of every query on stream and returns
+ *                   without waiting. The first run captures the launch
+ *                   sequence into a CUDA graph (on a private stream) and
+ *                   later runs replay it; where capture is unavailable the
+ *                   kernels are launched directly. Runs of one batch must not
+ *                   overlap on the GPU.
+ * eic_batch_wait    waits for stream, copies each query's status into
+ *                   statuses (host array of num_queries, or NULL) and
+ *                   returns the first non-OK one.
+ * eic_batch_tune    autotuner: runs the whole batch for group counts from
+ *                   the most down (divisors of the co-resident grid and
+ *                   powers of two) until two in a row are 20% slower than
+ *                   the best; then, at the best count, step-width scalings
+ *                   gap_shift + 1, + 2, ... while they help (up to 8),
+ *                   window-class thresholds heavy_min 64 and 256, and a
+ *                   256-thread block. Each configuration gets a warm-up run
+ *                   and, when that is within 2x of the best, a timed run
+ *                   (CUDA events on stream); the fastest is kept for later
+ *                   runs and the scratch shrinks to its group count. Every
+ *                   tried configuration computes the same exact distances;
+ *                   dists hold a complete result afterwards. best (or NULL)
+ *                   receives the chosen configuration. Synchronous.
+ * eic_batch_info    the current configuration.
+ * eic_batch_destroy frees the batch (NULL accepted); no run may be in flight.
+ */
+typedef struct eic_batch eic_batch;
+
+typedef struct {
+  uint32_t groups;            /* block groups running queries at the same time */
+  uint32_t blocks_per_group;
+  uint32_t block_threads;
+  uint32_t cuda_graph;        /* 1 when runs replay a captured CUDA graph */
+  uint32_t gap_shift;         /* step-width scaling in use (eic_params.gap_shift) */
+  uint32_t heavy_min;         /* window-class threshold in use (eic_params.heavy_min) */
+  uint32_t queries;
+  uint32_t reserved;
+  uint64_t scratch_bytes;     /* device bytes of the groups' scratch */
+  double tuned_ms;            /* fastest run seen by eic_batch_tune, 0 if not tuned */
+} eic_batch_config;
+
+int eic_batch_create(const eic_graph* const* graphs, const uint32_t* sources, uint32_t num_queries,
+                     uint32_t* const* dists, const eic_params* params, eic_batch** out);
+int eic_batch_run(eic_batch* b, void* stream);
+int eic_batch_wait(eic_batch* b, void* stream, int* statuses);
+int eic_batch_tune(eic_batch* b, void* stream, eic_batch_config* best);
+int eic_batch_info(const eic_batch* b, eic_batch_config* out);
+int eic_batch_destroy(eic_batch* b);
 
 /*
  * Allocation-free single-source query. The paper has no counterpart: this

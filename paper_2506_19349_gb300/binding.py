@@ -18,20 +18,29 @@ LIB_PATH = os.path.join(_HERE, "libeic.so")
 
 EIC_INF = 0xFFFFFFFF
 RATIO_NUM = 4096
-OK, EINVAL, ENOMEM, ECUDA, EOVERFLOW, ETIMEOUT, EBUSY, ESIZE = range(8)
+OK, EINVAL, ENOMEM, ECUDA, EOVERFLOW, ETIMEOUT, EBUSY, ESIZE, EABORT = range(9)
 NOALLOC_MAX_VERTICES = 1 << 18
 FLAG_NO_PULL = 1
 
 # Every name declared in include/eic.h.
 EXPORTS = ("eic_params_default", "eic_strerror", "eic_version", "eic_graph_create", "eic_graph_info",
            "eic_graph_export", "eic_graph_memory", "eic_graph_destroy", "eic_sssp", "eic_sssp_batch",
-           "eic_sssp_noalloc")
+           "eic_sssp_noalloc", "eic_batch_create", "eic_batch_run", "eic_batch_wait", "eic_batch_tune",
+           "eic_batch_info", "eic_batch_destroy")
 
 
 class Params(ctypes.Structure):
     _fields_ = [("alpha", ctypes.c_uint32), ("beta", ctypes.c_double), ("st_num", ctypes.c_uint32),
                 ("gap_shift", ctypes.c_uint32), ("block_threads", ctypes.c_uint32), ("heavy_min", ctypes.c_uint32),
-                ("max_spin_log2", ctypes.c_uint32), ("flags", ctypes.c_uint32), ("reserved", ctypes.c_uint32 * 8)]
+                ("max_spin_log2", ctypes.c_uint32), ("flags", ctypes.c_uint32), ("batch_groups", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32 * 7)]
+
+
+class BatchConfig(ctypes.Structure):
+    _fields_ = [("groups", ctypes.c_uint32), ("blocks_per_group", ctypes.c_uint32), ("block_threads", ctypes.c_uint32),
+                ("cuda_graph", ctypes.c_uint32), ("gap_shift", ctypes.c_uint32), ("heavy_min", ctypes.c_uint32),
+                ("queries", ctypes.c_uint32), ("reserved", ctypes.c_uint32), ("scratch_bytes", ctypes.c_uint64),
+                ("tuned_ms", ctypes.c_double)]
 
 
 class Step(ctypes.Structure):
@@ -46,7 +55,7 @@ class Stats(ctypes.Structure):
                 ("heavy", ctypes.c_uint64), ("pull_items", ctypes.c_uint64), ("trace", ctypes.POINTER(Step)),
                 ("trace_cap", ctypes.c_uint64),
                 ("trace_len", ctypes.c_uint64), ("timeline", ctypes.POINTER(ctypes.c_uint64)),
-                ("timeline_cap", ctypes.c_uint64), ("timeline_len", ctypes.c_uint64)]
+                ("timeline_cap", ctypes.c_uint64), ("timeline_len", ctypes.c_uint64), ("kernel_ms", ctypes.c_double)]
 
 
 class EicError(RuntimeError):
@@ -92,6 +101,19 @@ def load_library(path: str | None = None):
         L.eic_sssp_batch.restype = c_int
         L.eic_sssp_noalloc.argtypes = [vp, u32, vp, vp]
         L.eic_sssp_noalloc.restype = c_int
+        L.eic_batch_create.argtypes = [ctypes.POINTER(vp), vp, u32, ctypes.POINTER(vp), ctypes.POINTER(Params),
+                                       ctypes.POINTER(vp)]
+        L.eic_batch_create.restype = c_int
+        L.eic_batch_run.argtypes = [vp, vp]
+        L.eic_batch_run.restype = c_int
+        L.eic_batch_wait.argtypes = [vp, vp, vp]
+        L.eic_batch_wait.restype = c_int
+        L.eic_batch_tune.argtypes = [vp, vp, ctypes.POINTER(BatchConfig)]
+        L.eic_batch_tune.restype = c_int
+        L.eic_batch_info.argtypes = [vp, ctypes.POINTER(BatchConfig)]
+        L.eic_batch_info.restype = c_int
+        L.eic_batch_destroy.argtypes = [vp]
+        L.eic_batch_destroy.restype = c_int
         _lib = L
         return L
 
@@ -244,6 +266,58 @@ def sssp_batch(graphs, sources, dists, params: Params | None = None, stream=None
     L.eic_sssp_batch(harr, srcs.ctypes.data, q, darr, ctypes.byref(params) if params is not None else None,
                      statuses.ctypes.data, _stream_ptr(stream))
     return statuses
+
+
+def _config_dict(c: BatchConfig) -> dict:
+    return {f: getattr(c, f) for f, _ in BatchConfig._fields_ if f != "reserved"}
+
+
+class Batch:
+    """A prepared batch (eic_batch_*): queries (graphs[i], sources[i]) ->
+    dists[i] in one persistent launch, replayed as a CUDA graph."""
+
+    def __init__(self, graphs, sources, dists, params: Params | None = None):
+        L = load_library()
+        self._graphs = list(graphs)  # keep the graphs and outputs alive with the batch
+        self.dists = list(dists)
+        q = len(sources)
+        harr = (ctypes.c_void_p * q)(*[g.handle.value for g in self._graphs])
+        self._srcs = np.ascontiguousarray(sources, dtype=np.uint32)
+        darr = (ctypes.c_void_p * q)(*[d.data_ptr() for d in self.dists])
+        self._h = ctypes.c_void_p()
+        _check(L.eic_batch_create(harr, self._srcs.ctypes.data, q, darr,
+                                  ctypes.byref(params) if params is not None else None, ctypes.byref(self._h)),
+               "eic_batch_create")
+        self.n = q
+
+    def run(self, stream=None):
+        _check(load_library().eic_batch_run(self._h, _stream_ptr(stream)), "eic_batch_run")
+
+    def wait(self, stream=None) -> np.ndarray:
+        st = np.zeros(self.n, dtype=np.int32)
+        load_library().eic_batch_wait(self._h, _stream_ptr(stream), st.ctypes.data)
+        return st
+
+    def tune(self, stream=None) -> dict:
+        c = BatchConfig()
+        _check(load_library().eic_batch_tune(self._h, _stream_ptr(stream), ctypes.byref(c)), "eic_batch_tune")
+        return _config_dict(c)
+
+    def info(self) -> dict:
+        c = BatchConfig()
+        _check(load_library().eic_batch_info(self._h, ctypes.byref(c)), "eic_batch_info")
+        return _config_dict(c)
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value and _lib is not None:
+            _lib.eic_batch_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def to_host_u32(t) -> np.ndarray:

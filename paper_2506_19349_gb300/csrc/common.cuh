@@ -90,18 +90,20 @@ struct GridBarrier {
   uint32_t gen;
 };
 
-// Software grid barrier for a co-resident (cooperatively launched) grid.
-// Every wait is bounded: after max_spin polls the block records
-// EIC_ETIMEOUT in *status and all blocks leave at their next barrier. Returns
-// false when the kernel must stop (any block reported an error).
-__device__ __forceinline__ bool grid_barrier(GridBarrier* bar, uint32_t* gen_local, uint64_t max_spin, int* status) {
+// Software barrier over nblocks co-resident (cooperatively launched) blocks:
+// the whole grid, or one block group of it. Every wait is bounded: after
+// max_spin polls the block records EIC_ETIMEOUT in *status and all blocks
+// leave at their next barrier. Returns false when the blocks must stop (one
+// of them reported an error).
+__device__ __forceinline__ bool grid_barrier(GridBarrier* bar, uint32_t* gen_local, uint32_t nblocks, uint64_t max_spin,
+                                             int* status) {
   __shared__ int s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
     uint32_t g = *gen_local;
     __threadfence();
     uint32_t arrived = atomicAdd(&bar->count, 1u);
-    if (arrived == gridDim.x - 1) {
+    if (arrived == nblocks - 1) {
       bar->count = 0;
       __threadfence();
       atomicExch(&bar->gen, g + 1);

@@ -603,6 +603,7 @@ const char* eic_strerror(int status) {
     case EIC_ETIMEOUT: return "device wait timed out";
     case EIC_EBUSY: return "busy";
     case EIC_ESIZE: return "graph exceeds the limits of the allocation-free entry point";
+    case EIC_EABORT: return "not run: every block group of the batch stopped at an earlier error";
     default: return "unknown status";
   }
 }

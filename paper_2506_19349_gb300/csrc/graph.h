@@ -38,6 +38,7 @@ struct Ctl {
   uint32_t ub_cand;
   uint32_t tcnt[3];  // tasks of the round, by round id mod 3
   uint32_t s2_done;
+  uint32_t next_q;  // batch: the query the group's first block claimed
   uint32_t acc_maxd;
   unsigned long long acc_deg;
   uint32_t acc_any;
@@ -67,6 +68,7 @@ struct Workspace {
   unsigned long long* timeline = nullptr;
   Ctl* ctl = nullptr;
   Ctl* ctl_host = nullptr;  // pinned mirror for status readback
+  cudaEvent_t ev[2] = {nullptr, nullptr};  // around the query kernel, when statistics are asked for
   uint32_t ring_bits = 0, ring_shift = 0;
   uint32_t task_cap = 0, step_cap = 0;
   uint64_t bytes = 0;

@@ -33,6 +33,9 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
+#include <vector>
+
 #include "graph.h"
 #include "stats.cuh"
 
@@ -81,7 +84,11 @@ struct KArgs {
   uint32_t task_cap, step_cap, trace_cap;
   unsigned long long* timeline;  // NULL unless the caller asked for it
   uint32_t timeline_cap;
+  uint32_t nb;  // blocks working on this query: the grid, or one block group of a batch
 };
+
+// Index of the block within the blocks that work on its query.
+__device__ __forceinline__ uint32_t qblock(const KArgs& A) { return blockIdx.x % A.nb; }
 
 constexpr uint32_t kMaxBlock = 512;
 constexpr uint32_t kMaxWarps = kMaxBlock / 32;
@@ -168,7 +175,7 @@ __device__ __forceinline__ void tl_block(const KArgs& A, uint32_t kind, uint32_t
   uint32_t i = atomicAdd(&A.ctl->tl_len, 1u);
   if (i < A.timeline_cap) {
     A.timeline[2 * i] = t;
-    A.timeline[2 * i + 1] = ((unsigned long long)kind << 32) | ((unsigned long long)blockIdx.x << 48) | rid;
+    A.timeline[2 * i + 1] = ((unsigned long long)kind << 32) | ((unsigned long long)qblock(A) << 48) | rid;
   }
 }
 
@@ -327,7 +334,7 @@ __device__ void round_phase(const KArgs& A, const RoundCtx& R, const Local& L, R
   const uint32_t tid = threadIdx.x, nt = blockDim.x, lane = lane_id(), warp = tid >> 5;
   const uint32_t np = round1 ? L.push_end - L.push_beg : 0;
   const uint32_t npp = np + L.pull_cnt;
-  const uint32_t gwarp = blockIdx.x * (nt >> 5) + warp, nwarps = gridDim.x * (nt >> 5);
+  const uint32_t gwarp = qblock(A) * (nt >> 5) + warp, nwarps = A.nb * (nt >> 5);
   const int64_t pull_bound = R.ub - R.st;
   WarpScr& W = S.w[warp];
   for (uint32_t base = gwarp * 32; base < nitems; base += nwarps * 32) {
@@ -446,9 +453,9 @@ __device__ void round_phase(const KArgs& A, const RoundCtx& R, const Local& L, R
 __device__ void task_phase(const KArgs& A, const RoundCtx& R, uint32_t ntasks, Stage& T, Counters& C) {
   const uint32_t lane = lane_id();
   const uint32_t wpb = blockDim.x >> 5;
-  const uint32_t nwarps = gridDim.x * wpb;
+  const uint32_t nwarps = A.nb * wpb;
   const int64_t pull_bound = R.ub - R.st;
-  for (uint32_t t = blockIdx.x * wpb + (threadIdx.x >> 5); t < ntasks; t += nwarps) {
+  for (uint32_t t = qblock(A) * wpb + (threadIdx.x >> 5); t < ntasks; t += nwarps) {
     const Task tk = A.tasks[t];
     if (tk.d != kNone) {  // push
 #pragma unroll
@@ -781,15 +788,28 @@ __device__ __forceinline__ void block_sums(unsigned long long (&v)[K], unsigned 
   __syncthreads();
 }
 
-__global__ void __launch_bounds__(kMaxBlock, 2) k_eic(KArgs A) {
-  __shared__ PhaseScr P;
-  __shared__ Stage T;
-  __shared__ BState B;
-  __shared__ unsigned long long sh_red[32][7];
-  __shared__ unsigned long long sh_snap[4];
-  __shared__ uint32_t sh_last;
+// Shared-memory scratch of one block in the query loop.
+struct QueryShared {
+  PhaseScr P;
+  Stage T;
+  BState B;
+  unsigned long long red[32][7];
+  unsigned long long snap[4];
+  uint32_t last;
+};
+
+// The query loop of Algorithm 1 run by the A.nb blocks of one query: rounds
+// of a step (item phase, task phase), statistics pass, step boundary, until
+// termination. gen is the block's copy of the barrier generation.
+__device__ void run_query(const KArgs& A, QueryShared& Q, uint32_t& gen) {
+  PhaseScr& P = Q.P;
+  Stage& T = Q.T;
+  BState& B = Q.B;
+  auto& sh_red = Q.red;
+  auto& sh_snap = Q.snap;
+  uint32_t& sh_last = Q.last;
   Ctl* c = A.ctl;
-  uint32_t gen = __ldcg(&c->bar.gen);
+  const uint32_t qb = qblock(A);
   Local L;
   L.rid = 0;
   L.qsel = 0;
@@ -806,7 +826,7 @@ __global__ void __launch_bounds__(kMaxBlock, 2) k_eic(KArgs A) {
     B.highd_lb = A.G.highd0;
     B.j0 = 1;
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0) tl_mark(A, 0, L.rid);
+  if (qb == 0 && threadIdx.x == 0) tl_mark(A, 0, L.rid);
   bool alive = !L.done;  // an isolated source has nothing to relax
   uint32_t total_rounds = 0;
   constexpr uint32_t kMaxRounds = 1u << 22;  // every block counts the same rounds and stops together
@@ -822,14 +842,14 @@ __global__ void __launch_bounds__(kMaxBlock, 2) k_eic(KArgs A) {
       }
       const bool round1 = (L.step >= 2 && rin == 0);
       // counters of round rid+1 were last read two barriers ago: clear them now
-      if (blockIdx.x == 0 && threadIdx.x == 0) {
+      if (qb == 0 && threadIdx.x == 0) {
         c->qcnt[(L.rid + 1) % 3] = 0;
         c->tcnt[(L.rid + 1) % 3] = 0;
         c->work[(L.rid + 1) % 3] = 0;
       }
       {  // the other bitmap served round rid-1 and is next used in round rid+1: clear it now
         uint32_t* other = A.fbits + ((L.rid + 1) & 1u) * A.fwords;
-        for (uint32_t wi = blockIdx.x * blockDim.x + threadIdx.x; wi < A.fwords; wi += gridDim.x * blockDim.x)
+        for (uint32_t wi = qb * blockDim.x + threadIdx.x; wi < A.fwords; wi += A.nb * blockDim.x)
           __stcg(&other[wi], 0u);
       }
       RoundCtx R;
@@ -852,7 +872,7 @@ __global__ void __launch_bounds__(kMaxBlock, 2) k_eic(KArgs A) {
       if (!L.pull_on) LL.pull_cnt = 0;
       const uint32_t nitems = round1 ? (LL.push_end - LL.push_beg) + LL.pull_cnt + LL.extra_s : L.cur_cnt;
       round_phase(A, R, LL, P.r, T, nitems, round1, qin, C);
-      if (!grid_barrier(&c->bar, &gen, A.max_spin, &c->status)) {
+      if (!grid_barrier(&c->bar, &gen, A.nb, A.max_spin, &c->status)) {
         alive = false;
         break;
       }
@@ -860,7 +880,7 @@ __global__ void __launch_bounds__(kMaxBlock, 2) k_eic(KArgs A) {
         sh_snap[0] = __ldcg(&c->tcnt[L.rid % 3]);
         sh_snap[1] = __ldcg(&c->qcnt[L.rid % 3]);
         sh_snap[2] = __ldcg(&c->ub_cand);
-        if (blockIdx.x == 0) tl_mark(A, 1, L.rid);
+        if (qb == 0) tl_mark(A, 1, L.rid);
       }
       __syncthreads();
       const unsigned long long hp = sh_snap[0];
@@ -869,11 +889,11 @@ __global__ void __launch_bounds__(kMaxBlock, 2) k_eic(KArgs A) {
       __syncthreads();
       if (hp != 0) {
         task_phase(A, R, (uint32_t)hp, T, C);
-        if (!grid_barrier(&c->bar, &gen, A.max_spin, &c->status)) {
+        if (!grid_barrier(&c->bar, &gen, A.nb, A.max_spin, &c->status)) {
           alive = false;
           break;
         }
-        if (blockIdx.x == 0 && threadIdx.x == 0) tl_mark(A, 2, L.rid);
+        if (qb == 0 && threadIdx.x == 0) tl_mark(A, 2, L.rid);
         if (threadIdx.x == 0) {
           sh_snap[1] = __ldcg(&c->qcnt[L.rid % 3]);
           sh_snap[2] = __ldcg(&c->ub_cand);
@@ -906,8 +926,8 @@ __global__ void __launch_bounds__(kMaxBlock, 2) k_eic(KArgs A) {
       const uint32_t lend = (uint32_t)sh_snap[3];
       unsigned long long bdeg = 0;
       uint32_t bmax = 0, bany = 0;
-      const uint32_t nthreads = gridDim.x * blockDim.x;
-      for (uint32_t base = lbeg + blockIdx.x * blockDim.x; base < lend; base += nthreads) {
+      const uint32_t nthreads = A.nb * blockDim.x;
+      for (uint32_t base = lbeg + qb * blockDim.x; base < lend; base += nthreads) {
         const uint32_t idx = base + threadIdx.x;
         bool take = false;
         uint32_t x = 0, d = 0, xrb = 0, xre = 0;
@@ -985,11 +1005,11 @@ __global__ void __launch_bounds__(kMaxBlock, 2) k_eic(KArgs A) {
         __threadfence();
         atomicAdd(&c->s2_done, 1u);
       }
-      if (blockIdx.x == 0) {  // block 0 waits (bounded) for every block's statistics
+      if (qb == 0) {  // block 0 waits (bounded) for every block's statistics
         if (threadIdx.x == 0) {
           uint64_t spins = 0;
           sh_last = 1;
-          while (ld_acquire_u32(&c->s2_done) < gridDim.x) {
+          while (ld_acquire_u32(&c->s2_done) < A.nb) {
             if (ld_volatile_int(&c->status) != 0 || ++spins > A.max_spin) {
               atomicCAS(&c->status, 0, EIC_ETIMEOUT);
               sh_last = 0;
@@ -1004,63 +1024,76 @@ __global__ void __launch_bounds__(kMaxBlock, 2) k_eic(KArgs A) {
         if (threadIdx.x == 0) tl_mark(A, 5, L.rid);
       }
     }
-    if (!grid_barrier(&c->bar, &gen, A.max_spin, &c->status)) break;
-    if (blockIdx.x == 0 && threadIdx.x == 0) tl_mark(A, 3, L.rid);
+    if (!grid_barrier(&c->bar, &gen, A.nb, A.max_spin, &c->status)) break;
+    if (qb == 0 && threadIdx.x == 0) tl_mark(A, 3, L.rid);
     read_ctl(c, L);
     if (L.done) break;
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0 && A.status_out) *A.status_out = ld_volatile_int(&c->status);
+  if (qb == 0 && threadIdx.x == 0 && A.status_out) *A.status_out = ld_volatile_int(&c->status);
+}
+
+__global__ void __launch_bounds__(kMaxBlock, 2) k_eic(KArgs A) {
+  __shared__ QueryShared Q;
+  uint32_t gen = __ldcg(&A.ctl->bar.gen);
+  run_query(A, Q, gen);
+}
+
+// Control block of a new query (one thread): the source's distance, the
+// first round's frontier {s}, step 1 = <0, +inf> with st = 0, and gap(0).
+__device__ void ctl_init(const KArgs& A) {
+  Ctl* c = A.ctl;
+  const DevGraph& G = A.G;
+  const uint32_t si = G.orig2int[A.s];
+  c->s_int = si;
+  uint32_t dgs = 0;
+  if (si != EIC_INF) {
+    A.dist[si] = 0;
+    A.q0[0] = si;
+    A.touched[0] = si;
+    dgs = G.row[si + 1] - G.row[si];
+  }
+  A.step_off[1] = 0;
+  A.step_ub[0] = 0;
+  c->lb = 0;
+  c->ub = EIC_INF_T;
+  c->st = 0;
+  c->lb0 = 0;
+  c->step = 1;
+  c->done = si == EIC_INF ? 1u : 0u;
+  c->push_beg = c->push_end = 0;
+  c->pull_on = c->pull_cnt = c->extra_s = 0;
+  c->step_off_cur = 0;
+  c->st0 = -1;
+  c->st1 = -1;
+  c->sumd_lb = G.two_m;
+  c->highd_lb = G.highd0;
+  c->gap_lb = dev_gap(G.two_m, G.highd0, G.two_m, A.alpha, A.beta, G.rtow);
+  c->max_settled = -1;
+  c->rounds_in_step = 0;
+  c->trace_len = 0;
+  c->tl_len = 0;
+  c->qcnt[0] = c->qcnt[1] = c->qcnt[2] = 0;
+  c->work[0] = c->work[1] = c->work[2] = 0;
+  c->settled_cnt = 0;
+  c->touched_cnt = 1;
+  c->ub_cand = (G.highd0 > 0 && dgs >= G.highd0) ? 0u : EIC_INF;
+  c->tcnt[0] = c->tcnt[1] = c->tcnt[2] = 0;
+  c->s2_done = 0;
+  c->acc_maxd = 0;
+  c->acc_deg = 0;
+  c->acc_any = 0;
+  c->cnt_rounds = c->cnt_frontier = c->cnt_trav = c->cnt_pulls = c->cnt_improved = c->cnt_heavy = 0;
+  c->cnt_pitems = 0;
 }
 
 __global__ void k_init(KArgs A) {
-  Ctl* c = A.ctl;
   const DevGraph& G = A.G;
   for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < G.D; r += gridDim.x * blockDim.x) A.hist[r] = G.dcnt0[r];
   for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r <= A.ring_mask; r += gridDim.x * blockDim.x) A.ring[r] = 0;
   if (blockIdx.x == 0 && threadIdx.x == 0) {
-    const uint32_t si = G.orig2int[A.s];
-    c->s_int = si;
-    uint32_t dgs = 0;
-    if (si != EIC_INF) {
-      A.dist[si] = 0;
-      A.q0[0] = si;
-      A.touched[0] = si;
-      dgs = G.row[si + 1] - G.row[si];
-    }
-    A.step_off[1] = 0;
-    A.step_ub[0] = 0;
-    c->lb = 0;
-    c->ub = EIC_INF_T;
-    c->st = 0;
-    c->lb0 = 0;
-    c->step = 1;
-    c->done = si == EIC_INF ? 1u : 0u;
-    c->push_beg = c->push_end = 0;
-    c->pull_on = c->pull_cnt = c->extra_s = 0;
-    c->step_off_cur = 0;
-    c->st0 = -1;
-    c->st1 = -1;
-    c->sumd_lb = G.two_m;
-    c->highd_lb = G.highd0;
-    c->gap_lb = dev_gap(G.two_m, G.highd0, G.two_m, A.alpha, A.beta, G.rtow);
-    c->max_settled = -1;
-    c->rounds_in_step = 0;
-    c->trace_len = 0;
-    c->tl_len = 0;
-    c->qcnt[0] = c->qcnt[1] = c->qcnt[2] = 0;
-    c->work[0] = c->work[1] = c->work[2] = 0;
-    c->settled_cnt = 0;
-    c->touched_cnt = 1;
-    c->ub_cand = (G.highd0 > 0 && dgs >= G.highd0) ? 0u : EIC_INF;
-    c->tcnt[0] = c->tcnt[1] = c->tcnt[2] = 0;
-    c->s2_done = 0;
-    c->acc_maxd = 0;
-    c->acc_deg = 0;
-    c->acc_any = 0;
-    c->cnt_rounds = c->cnt_frontier = c->cnt_trav = c->cnt_pulls = c->cnt_improved = c->cnt_heavy = 0;
-    c->cnt_pitems = 0;
-    c->bar.count = 0;
-    c->status = 0;
+    ctl_init(A);
+    A.ctl->bar.count = 0;
+    A.ctl->status = 0;
   }
 }
 
@@ -1097,6 +1130,163 @@ __global__ void k_parent(DevGraph G, const uint32_t* __restrict__ idist, uint32_
     }
     if (lane == 0) parent[v] = v == s ? s : best;
   }
+}
+
+// ------------------------------------------------------------- batched queries
+
+// One query of a batch: graph, caller's output buffer, source, and the
+// graph-dependent layout of the statistics ring and task list.
+struct BatchQuery {
+  DevGraph G;
+  uint32_t* out;
+  uint32_t s;
+  uint32_t ring_mask, ring_shift, task_cap;
+};
+
+// Scratch of one block group, reused by every query the group runs.
+struct BatchSlot {
+  uint32_t* idist;
+  uint32_t* fbits;
+  uint32_t* cursor;
+  uint32_t* q0;
+  uint32_t* q1;
+  uint32_t* sid;
+  uint32_t* sd;
+  uint32_t* scur;
+  uint2* srow;
+  uint32_t* touched;
+  uint32_t* sbits;
+  uint32_t* hist;
+  unsigned long long* ring;
+  Task* tasks;
+  int64_t* step_ub;
+  uint32_t* step_off;
+  Ctl* ctl;
+};
+
+struct BatchArgs {
+  const BatchQuery* q;    // [nq], in the order groups claim them
+  const BatchSlot* slot;  // [gridDim.x / nb]
+  int* status;            // [nq]; a query no group finished keeps EIC_EABORT
+  uint32_t* queue;        // next unclaimed query
+  uint32_t nq, nb;        // queries; blocks per group
+  uint32_t alpha;
+  double beta;
+  uint32_t st_num, gap_shift, heavy_min, flags, step_cap;
+  uint64_t max_spin;
+};
+
+// The query's scratch at its starting values (what the single-query path
+// does with memsets and k_init), by the group's blocks.
+__device__ bool query_setup(const KArgs& A, uint32_t& gen) {
+  const DevGraph& G = A.G;
+  const uint32_t stride = A.nb * blockDim.x, t0 = qblock(A) * blockDim.x + threadIdx.x;
+  for (uint32_t i = t0; i < G.ni; i += stride) __stcg(&A.dist[i], EIC_INF);
+  for (uint32_t i = t0; i < 2 * A.fwords; i += stride) __stcg(&A.fbits[i], 0u);
+  for (uint32_t i = t0; i < A.fwords; i += stride) __stcg(&A.sbits[i], 0u);
+  for (uint32_t r = t0; r < G.D; r += stride) __stcg(&A.hist[r], __ldg(&G.dcnt0[r]));
+  for (uint32_t r = t0; r <= A.ring_mask; r += stride) __stcg(&A.ring[r], 0ull);
+  if (!grid_barrier(&A.ctl->bar, &gen, A.nb, A.max_spin, &A.ctl->status)) return false;
+  if (qblock(A) == 0 && threadIdx.x == 0) ctl_init(A);
+  return grid_barrier(&A.ctl->bar, &gen, A.nb, A.max_spin, &A.ctl->status);
+}
+
+// Distances in the caller's numbering (as k_output), by the group's blocks.
+__device__ void query_output(const KArgs& A) {
+  const DevGraph& G = A.G;
+  const uint64_t stride = (uint64_t)A.nb * blockDim.x;
+  for (uint64_t u = (uint64_t)qblock(A) * blockDim.x + threadIdx.x; u < G.n; u += stride) {
+    const uint32_t i = __ldg(&G.orig2int[u]);
+    A.out[u] = u == A.s ? 0u : (i == EIC_INF ? EIC_INF : __ldcg(&A.dist[i]));
+  }
+}
+
+// Many queries in one cooperative launch. The grid is cut into groups of nb
+// blocks; each group claims the next query from a device counter, runs it
+// with its own scratch and a barrier over its nb blocks, writes the output,
+// and claims again. A group stops at its first query with a non-OK status
+// (its barrier state is then unreliable); the other groups carry on.
+__global__ void __launch_bounds__(kMaxBlock, 2) k_eic_batch(BatchArgs P) {
+  __shared__ QueryShared Q;
+  __shared__ KArgs sA;
+  __shared__ uint32_t sh_qi;
+  const uint32_t grp = blockIdx.x / P.nb, qb = blockIdx.x % P.nb;
+  const BatchSlot& W = P.slot[grp];
+  Ctl* c = W.ctl;
+  uint32_t gen = __ldcg(&c->bar.gen);
+  uint32_t qi = 0xFFFFFFFFu;
+  for (;;) {
+    if (qb == 0 && threadIdx.x == 0) c->next_q = ld_volatile_int(&c->status) == 0 ? atomicAdd(P.queue, 1u) : P.nq;
+    if (!grid_barrier(&c->bar, &gen, P.nb, P.max_spin, &c->status)) break;
+    if (threadIdx.x == 0) sh_qi = __ldcg(&c->next_q);
+    __syncthreads();
+    qi = sh_qi;
+    if (qi >= P.nq) break;
+    if (threadIdx.x == 0) {
+      const BatchQuery& bq = P.q[qi];
+      sA.G = bq.G;
+      sA.dist = W.idist;
+      sA.out = bq.out;
+      sA.fbits = W.fbits;
+      sA.fwords = bq.G.ni / 32 + 2;
+      sA.cursor = W.cursor;
+      sA.q0 = W.q0;
+      sA.q1 = W.q1;
+      sA.sid = W.sid;
+      sA.sd = W.sd;
+      sA.scur = W.scur;
+      sA.srow = W.srow;
+      sA.touched = W.touched;
+      sA.sbits = W.sbits;
+      sA.hist = W.hist;
+      sA.ring = W.ring;
+      sA.tasks = W.tasks;
+      sA.step_ub = W.step_ub;
+      sA.step_off = W.step_off;
+      sA.trace = nullptr;
+      sA.ctl = c;
+      sA.status_out = &P.status[qi];
+      sA.s = bq.s;
+      sA.alpha = P.alpha;
+      sA.beta = P.beta;
+      sA.st_num = P.st_num;
+      sA.gap_shift = P.gap_shift;
+      sA.heavy_min = P.heavy_min;
+      sA.max_spin = P.max_spin;
+      sA.flags = P.flags;
+      sA.ring_mask = bq.ring_mask;
+      sA.ring_shift = bq.ring_shift;
+      sA.task_cap = bq.task_cap;
+      sA.step_cap = P.step_cap;
+      sA.trace_cap = 0;
+      sA.timeline = nullptr;
+      sA.timeline_cap = 0;
+      sA.nb = P.nb;
+    }
+    __syncthreads();
+    if (!query_setup(sA, gen)) break;
+    run_query(sA, Q, gen);
+    __syncthreads();
+    if (ld_volatile_int(&c->status) != 0) break;
+    query_output(sA);
+  }
+  // the query a group stopped in reports the group's status
+  if (qb == 0 && threadIdx.x == 0 && qi < P.nq) {
+    const int st = ld_volatile_int(&c->status);
+    if (st != 0) P.status[qi] = st;
+  }
+}
+
+// Starting state of every group's barrier and status, of the work queue and
+// of the per-query statuses (EIC_EABORT until a group finishes the query).
+__global__ void k_batch_prep(BatchArgs P, uint32_t groups) {
+  const uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g < groups) {
+    P.slot[g].ctl->bar.count = 0;
+    P.slot[g].ctl->status = 0;
+  }
+  if (g < P.nq) P.status[g] = EIC_EABORT;
+  if (g == 0) *P.queue = 0;
 }
 
 }  // namespace
@@ -1209,12 +1399,13 @@ KArgs make_args(eic_graph* g, uint32_t s, uint32_t* dist, const eic_params& p, i
   A.trace_cap = kTraceCap;
   A.timeline = nullptr;
   A.timeline_cap = 0;
+  A.nb = (uint32_t)w.grid;
   return A;
 }
 
 // Enqueue one query: dist <- +inf, init, persistent kernel, optional parent.
 int enqueue_query(eic_graph* g, uint32_t s, uint32_t* dist, uint32_t* parent, const eic_params& p, int* status_out,
-                  cudaStream_t st, bool timeline = false) {
+                  cudaStream_t st, bool timeline = false, cudaEvent_t ev0 = nullptr, cudaEvent_t ev1 = nullptr) {
   Workspace& w = g->ws;
   const int block = p.block_threads ? (int)p.block_threads : kDefaultBlock;
   int rc = launch_shape(&w, block);
@@ -1230,7 +1421,9 @@ int enqueue_query(eic_graph* g, uint32_t s, uint32_t* dist, uint32_t* parent, co
   k_init<<<64, 256, 0, st>>>(A);
   EIC_CUDA_TRY(cudaGetLastError());
   void* args[] = {&A};
+  if (ev0) EIC_CUDA_TRY(cudaEventRecord(ev0, st));
   EIC_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)k_eic, dim3(w.grid), dim3(block), args, 0, st));
+  if (ev1) EIC_CUDA_TRY(cudaEventRecord(ev1, st));
   k_output<<<2 * w.grid, 256, 0, st>>>(g->dg, w.idist, s, dist);
   EIC_CUDA_TRY(cudaGetLastError());
   if (parent) {
@@ -1275,6 +1468,8 @@ void eic_ws_free(Workspace* w) {
   cudaFree(w->timeline);
   cudaFree(w->ctl);
   if (w->ctl_host) cudaFreeHost(w->ctl_host);
+  if (w->ev[0]) cudaEventDestroy(w->ev[0]);
+  if (w->ev[1]) cudaEventDestroy(w->ev[1]);
   *w = Workspace();
 }
 
@@ -1319,13 +1514,6 @@ int eic_ws_ensure(eic_graph* g, int) {
 
 namespace {
 constexpr int kMaxDevices = 64;
-struct BatchBuffers {  // per-device status arrays of eic_sssp_batch, kept for reuse
-  int* dstat = nullptr;
-  int* hstat = nullptr;
-  uint32_t cap = 0;
-};
-BatchBuffers g_batch[kMaxDevices];
-std::mutex g_batch_mu;
 }  // namespace
 
 extern "C" {
@@ -1355,12 +1543,19 @@ int eic_sssp(const eic_graph* gc, uint32_t source, uint32_t* dist, uint32_t* par
   }
   if (g->dg.two_m == 0) return trivial_query(g, source, dist, parent, st);
   if ((rc = eic_ws_ensure(g, 0))) return rc;
-  if ((rc = enqueue_query(g, source, dist, parent, p, nullptr, st, tl && tl_cap))) {
+  Workspace& w = g->ws;
+  if (stats && !w.ev[0]) {
+    if (cudaEventCreate(&w.ev[0]) != cudaSuccess || cudaEventCreate(&w.ev[1]) != cudaSuccess) {
+      (void)cudaGetLastError();
+      return EIC_ECUDA;
+    }
+  }
+  if ((rc = enqueue_query(g, source, dist, parent, p, nullptr, st, tl && tl_cap, stats ? w.ev[0] : nullptr,
+                          stats ? w.ev[1] : nullptr))) {
     cudaStreamSynchronize(st);
     (void)cudaGetLastError();
     return rc;
   }
-  Workspace& w = g->ws;
   EIC_CUDA_TRY(cudaMemcpyAsync(w.ctl_host, w.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
   EIC_CUDA_TRY(cudaStreamSynchronize(st));
   const Ctl& h = *w.ctl_host;
@@ -1374,6 +1569,9 @@ int eic_sssp(const eic_graph* gc, uint32_t source, uint32_t* dist, uint32_t* par
     stats->heavy = h.cnt_heavy;
     stats->pull_items = h.cnt_pitems;
     stats->trace_len = h.trace_len;
+    float kms = 0.f;
+    if (cudaEventElapsedTime(&kms, w.ev[0], w.ev[1]) == cudaSuccess) stats->kernel_ms = kms;
+    (void)cudaGetLastError();
     if (trace && trace_cap) {
       uint64_t rows = h.trace_len < trace_cap ? h.trace_len : trace_cap;
       if (rows > kTraceCap) rows = kTraceCap;
@@ -1389,70 +1587,560 @@ int eic_sssp(const eic_graph* gc, uint32_t source, uint32_t* dist, uint32_t* par
   return h.status;
 }
 
+}  // extern "C"
+
+// ------------------------------------------------------------ batch host side
+
+namespace {
+
+constexpr uint32_t kBatchStepCap = 1u << 17;  // steps per query of a batch
+constexpr double kBatchMemFrac = 0.8;         // share of free device memory the scratch may take
+
+// Capacities one block group's scratch must cover.
+struct SlotCaps {
+  uint64_t ni = 0, two_m = 0;
+  uint32_t D = 0, ring_bits = 0;
+  bool covers(const SlotCaps& o) const {
+    return ni >= o.ni && two_m >= o.two_m && D >= o.D && ring_bits >= o.ring_bits;
+  }
+};
+
+// Byte offsets of one group's arrays inside its slot (256-byte aligned).
+struct SlotLayout {
+  uint64_t idist, fbits, cursor, q0, q1, sid, sd, scur, srow, touched, sbits, hist, ring, tasks, step_ub, step_off,
+      ctl, bytes;
+};
+
+SlotLayout slot_layout(const SlotCaps& c) {
+  SlotLayout L;
+  uint64_t o = 0;
+  auto take = [&o](uint64_t bytes) {
+    const uint64_t at = o;
+    o += (bytes + 255) & ~255ull;
+    return at;
+  };
+  const uint64_t n = c.ni, words = n / 32 + 2;
+  L.idist = take(n * 4);
+  L.fbits = take(2 * words * 4);
+  L.cursor = take(n * 4);
+  L.q0 = take(n * 4);
+  L.q1 = take(n * 4);
+  L.sid = take((n + 2) * 4);
+  L.sd = take((n + 2) * 4);
+  L.scur = take((n + 2) * 4);
+  L.srow = take((n + 2) * 8);
+  L.touched = take((n + 1) * 4);
+  L.sbits = take(words * 4);
+  L.hist = take(((uint64_t)c.D + 1) * 4);
+  L.ring = take((1ull << c.ring_bits) * 8);
+  L.tasks = take((c.two_m / kHeavyMinFloor + 2) * sizeof(Task));
+  L.step_ub = take(((uint64_t)kBatchStepCap + 2) * 8);
+  L.step_off = take(((uint64_t)kBatchStepCap + 2) * 4);
+  L.ctl = take(sizeof(Ctl));
+  L.bytes = o;
+  return L;
+}
+
+// Scratch of `count` block groups in one device allocation.
+struct SlotPool {
+  unsigned char* base = nullptr;
+  BatchSlot* d_slots = nullptr;
+  SlotCaps caps;
+  uint32_t count = 0;
+  uint64_t slot_bytes = 0;
+
+  void release() {
+    cudaFree(base);
+    cudaFree(d_slots);
+    base = nullptr;
+    d_slots = nullptr;
+    caps = SlotCaps();
+    count = 0;
+    slot_bytes = 0;
+  }
+
+  int ensure(const SlotCaps& need, uint32_t groups) {
+    if (base && count >= groups && caps.covers(need)) return EIC_OK;
+    release();
+    const SlotLayout L = slot_layout(need);
+    if (cudaMalloc((void**)&base, L.bytes * groups) != cudaSuccess ||
+        cudaMalloc((void**)&d_slots, sizeof(BatchSlot) * groups) != cudaSuccess) {
+      (void)cudaGetLastError();
+      release();
+      return EIC_ENOMEM;
+    }
+    std::vector<BatchSlot> h(groups);
+    for (uint32_t g = 0; g < groups; ++g) {
+      unsigned char* b = base + (uint64_t)g * L.bytes;
+      BatchSlot& s = h[g];
+      s.idist = (uint32_t*)(b + L.idist);
+      s.fbits = (uint32_t*)(b + L.fbits);
+      s.cursor = (uint32_t*)(b + L.cursor);
+      s.q0 = (uint32_t*)(b + L.q0);
+      s.q1 = (uint32_t*)(b + L.q1);
+      s.sid = (uint32_t*)(b + L.sid);
+      s.sd = (uint32_t*)(b + L.sd);
+      s.scur = (uint32_t*)(b + L.scur);
+      s.srow = (uint2*)(b + L.srow);
+      s.touched = (uint32_t*)(b + L.touched);
+      s.sbits = (uint32_t*)(b + L.sbits);
+      s.hist = (uint32_t*)(b + L.hist);
+      s.ring = (unsigned long long*)(b + L.ring);
+      s.tasks = (Task*)(b + L.tasks);
+      s.step_ub = (int64_t*)(b + L.step_ub);
+      s.step_off = (uint32_t*)(b + L.step_off);
+      s.ctl = (Ctl*)(b + L.ctl);
+      if (cudaMemset(s.ctl, 0, sizeof(Ctl)) != cudaSuccess) {
+        (void)cudaGetLastError();
+        release();
+        return EIC_ECUDA;
+      }
+    }
+    if (cudaMemcpy(d_slots, h.data(), sizeof(BatchSlot) * groups, cudaMemcpyHostToDevice) != cudaSuccess) {
+      (void)cudaGetLastError();
+      release();
+      return EIC_ECUDA;
+    }
+    caps = need;
+    count = groups;
+    slot_bytes = L.bytes;
+    return EIC_OK;
+  }
+};
+
+uint32_t ring_layout(uint32_t maxw, uint32_t* shift) {
+  const uint32_t m = maxw ? maxw : 1;
+  uint32_t bits = 0;
+  while (bits < 32 && (1ull << bits) <= m) ++bits;  // 2^bits > maxW
+  *shift = bits > 20 ? bits - 20 : 0;
+  return bits < 20 ? bits : 20;
+}
+
+int batch_grid(int block, uint32_t* grid) {
+  int dev = 0, sms = 0, per_sm = 0, coop = 0;
+  EIC_CUDA_TRY(cudaGetDevice(&dev));
+  EIC_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  EIC_CUDA_TRY(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
+  if (!coop) return EIC_ECUDA;
+  EIC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_eic_batch, block, 0));
+  if (per_sm < 1) return EIC_ECUDA;
+  *grid = (uint32_t)(sms * per_sm);
+  return EIC_OK;
+}
+
+SlotPool g_pool[kMaxDevices];  // scratch reused by eic_sssp_batch, per device
+std::mutex g_pool_mu;
+
+}  // namespace
+
+// A prepared batch: the query table in claim order (largest graphs first),
+// the trivial queries (graphs without edges), the launch configuration and,
+// once run, the CUDA graph that replays it.
+struct eic_batch {
+  int device = 0;
+  uint32_t nq = 0;
+  eic_params p{};
+  std::vector<uint32_t> order;  // claim position -> caller's query index
+  std::vector<BatchQuery> hq;
+  struct Trivial {
+    uint32_t* dist;
+    uint32_t n, s, index;
+  };
+  std::vector<Trivial> trivial;
+  SlotCaps caps;
+  uint32_t groups = 0, nb = 0, block = 0, grid_max = 0;
+  SlotPool own;
+  SlotPool* pool = &own;
+  BatchQuery* d_q = nullptr;
+  int* d_status = nullptr;
+  int* h_status = nullptr;
+  uint32_t* d_queue = nullptr;
+  bool use_graph = true;
+  cudaGraphExec_t exec = nullptr;
+  double tuned_ms = 0.0;
+};
+
+namespace {
+
+// Largest group count whose scratch fits in the share of free memory.
+uint32_t groups_that_fit(eic_batch* b, uint32_t want) {
+  size_t fr = 0, tot = 0;
+  if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return want;
+  }
+  const uint64_t per = slot_layout(b->caps).bytes;
+  const uint64_t held = b->pool->base ? (uint64_t)b->pool->count * b->pool->slot_bytes : 0;
+  const uint64_t avail = (uint64_t)((double)(fr + held) * kBatchMemFrac);
+  const uint64_t fit = per ? avail / per : want;
+  return (uint32_t)(fit < want ? fit : want);
+}
+
+// groups -> blocks per group for the current block shape.
+int batch_configure(eic_batch* b, uint32_t groups, uint32_t block) {
+  uint32_t gmax = 0;
+  int rc = batch_grid((int)block, &gmax);
+  if (rc) return rc;
+  const uint32_t nrun = (uint32_t)b->hq.size();
+  if (groups == 0) {  // library choice: about 8 blocks per group, more for graphs above 2^27 entries
+    const uint64_t per = b->caps.two_m >> 24;
+    const uint32_t nb = per < 8 ? 8 : (per > gmax ? gmax : (uint32_t)per);
+    groups = gmax / nb;
+  }
+  if (groups > nrun) groups = nrun ? nrun : 1;
+  if (groups > gmax) groups = gmax;
+  groups = groups_that_fit(b, groups);
+  if (groups == 0) return EIC_ENOMEM;
+  if ((rc = b->pool->ensure(b->caps, groups))) return rc;
+  if (b->exec && (b->groups != groups || b->block != block)) {
+    cudaGraphExecDestroy(b->exec);
+    b->exec = nullptr;
+  }
+  b->groups = groups;
+  b->block = block;
+  b->grid_max = gmax;
+  b->nb = gmax / groups;
+  return EIC_OK;
+}
+
+BatchArgs batch_args(const eic_batch* b) {
+  BatchArgs P;
+  P.q = b->d_q;
+  P.slot = b->pool->d_slots;
+  P.status = b->d_status;
+  P.queue = b->d_queue;
+  P.nq = (uint32_t)b->hq.size();
+  P.nb = b->nb;
+  P.alpha = b->p.alpha;
+  P.beta = b->p.beta;
+  P.st_num = b->p.st_num;
+  P.gap_shift = b->p.gap_shift;
+  P.heavy_min = b->p.heavy_min;
+  P.flags = b->p.flags;
+  P.step_cap = kBatchStepCap;
+  P.max_spin = 1ull << b->p.max_spin_log2;
+  return P;
+}
+
+int batch_enqueue(eic_batch* b, cudaStream_t st) {
+  if (!b->hq.empty()) {
+    BatchArgs P = batch_args(b);
+    const uint32_t nrun = P.nq, cover = b->groups > nrun ? b->groups : nrun;
+    k_batch_prep<<<(cover + 255) / 256, 256, 0, st>>>(P, b->groups);
+    EIC_CUDA_TRY(cudaGetLastError());
+    void* args[] = {&P};
+    EIC_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)k_eic_batch, dim3(b->groups * b->nb), dim3(b->block), args,
+                                             0, st));
+  }
+  for (const auto& t : b->trivial) {  // no edges: only the source is reachable
+    EIC_CUDA_TRY(cudaMemsetAsync(t.dist, 0xFF, (uint64_t)t.n * 4, st));
+    EIC_CUDA_TRY(cudaMemsetAsync(t.dist + t.s, 0, 4, st));
+  }
+  return EIC_OK;
+}
+
+void batch_free(eic_batch* b) {
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  b->own.release();
+  cudaFree(b->d_q);
+  cudaFree(b->d_status);
+  cudaFree(b->d_queue);
+  if (b->h_status) cudaFreeHost(b->h_status);
+  delete b;
+}
+
+int batch_create(const eic_graph* const* graphs, const uint32_t* sources, uint32_t nq, uint32_t* const* dists,
+                 const eic_params* params, SlotPool* shared_pool, eic_batch** out) {
+  *out = nullptr;
+  if (nq == 0 || !graphs || !sources || !dists) return EIC_EINVAL;
+  eic_params p;
+  int rc = resolve_params(params, &p);
+  if (rc) return rc;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return EIC_ECUDA;
+  }
+  for (uint32_t i = 0; i < nq; ++i)
+    if (!graphs[i] || !dists[i] || sources[i] >= graphs[i]->dg.n || graphs[i]->device != dev) return EIC_EINVAL;
+  eic_batch* b = new eic_batch();
+  b->device = dev;
+  b->nq = nq;
+  b->p = p;
+  if (shared_pool) b->pool = shared_pool;
+  std::vector<uint32_t> idx;
+  for (uint32_t i = 0; i < nq; ++i) {
+    const DevGraph& G = graphs[i]->dg;
+    if (G.two_m == 0) {
+      b->trivial.push_back({dists[i], G.n, sources[i], i});
+      continue;
+    }
+    idx.push_back(i);
+  }
+  // largest graphs are claimed first (longest-processing-time order)
+  std::stable_sort(idx.begin(), idx.end(),
+                   [&](uint32_t a, uint32_t c) { return graphs[a]->dg.two_m > graphs[c]->dg.two_m; });
+  for (uint32_t i : idx) {
+    const DevGraph& G = graphs[i]->dg;
+    BatchQuery q;
+    q.G = G;
+    q.out = dists[i];
+    q.s = sources[i];
+    uint32_t shift = 0;
+    const uint32_t bits = ring_layout(G.maxw, &shift);
+    q.ring_mask = (1u << bits) - 1u;
+    q.ring_shift = shift;
+    q.task_cap = (uint32_t)(G.two_m / kHeavyMinFloor + 2);
+    b->hq.push_back(q);
+    b->order.push_back(i);
+    SlotCaps& c = b->caps;
+    c.ni = G.ni > c.ni ? G.ni : c.ni;
+    c.two_m = G.two_m > c.two_m ? G.two_m : c.two_m;
+    c.D = G.D > c.D ? G.D : c.D;
+    c.ring_bits = bits > c.ring_bits ? bits : c.ring_bits;
+  }
+  const uint64_t nrun = b->hq.size();
+  if (nrun) {
+    if (cudaMalloc((void**)&b->d_q, nrun * sizeof(BatchQuery)) != cudaSuccess ||
+        cudaMalloc((void**)&b->d_status, nrun * sizeof(int)) != cudaSuccess ||
+        cudaMalloc((void**)&b->d_queue, sizeof(uint32_t)) != cudaSuccess ||
+        cudaMallocHost((void**)&b->h_status, nrun * sizeof(int)) != cudaSuccess) {
+      (void)cudaGetLastError();
+      batch_free(b);
+      return EIC_ENOMEM;
+    }
+    if (cudaMemcpy(b->d_q, b->hq.data(), nrun * sizeof(BatchQuery), cudaMemcpyHostToDevice) != cudaSuccess) {
+      (void)cudaGetLastError();
+      batch_free(b);
+      return EIC_ECUDA;
+    }
+    const uint32_t block = p.block_threads ? p.block_threads : (uint32_t)kDefaultBlock;
+    if ((rc = batch_configure(b, p.batch_groups, block))) {
+      batch_free(b);
+      return rc;
+    }
+  }
+  *out = b;
+  return EIC_OK;
+}
+
+int batch_run(eic_batch* b, cudaStream_t st) {
+  if (b->use_graph && !b->exec) {  // capture the launch sequence once, replay it afterwards
+    cudaStream_t cs = nullptr;
+    cudaGraph_t graph = nullptr;
+    bool ok = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+    if (ok) {
+      const int rc = batch_enqueue(b, cs);
+      ok = cudaStreamEndCapture(cs, &graph) == cudaSuccess && rc == EIC_OK && graph &&
+           cudaGraphInstantiate(&b->exec, graph, 0) == cudaSuccess;
+    }
+    if (graph) cudaGraphDestroy(graph);
+    if (cs) cudaStreamDestroy(cs);
+    if (!ok) {  // capture unavailable: launch directly from now on
+      (void)cudaGetLastError();
+      b->exec = nullptr;
+      b->use_graph = false;
+    }
+  }
+  if (b->exec) {
+    EIC_CUDA_TRY(cudaGraphLaunch(b->exec, st));
+    return EIC_OK;
+  }
+  return batch_enqueue(b, st);
+}
+
+int batch_wait(eic_batch* b, cudaStream_t st, int* statuses) {
+  const uint64_t nrun = b->hq.size();
+  if (nrun) EIC_CUDA_TRY(cudaMemcpyAsync(b->h_status, b->d_status, nrun * sizeof(int), cudaMemcpyDeviceToHost, st));
+  EIC_CUDA_TRY(cudaStreamSynchronize(st));
+  std::vector<int> all(b->nq, EIC_OK);
+  for (uint64_t k = 0; k < nrun; ++k) all[b->order[k]] = b->h_status[k];
+  int first = EIC_OK;
+  for (uint32_t i = 0; i < b->nq; ++i) {
+    if (statuses) statuses[i] = all[i];
+    if (first == EIC_OK) first = all[i];
+  }
+  return first;
+}
+
+// Device time of one whole batch run (ms), or a negative value on error.
+double batch_time(eic_batch* b, cudaStream_t st) {
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return -1.0;
+  }
+  double ms = -1.0;
+  float t = 0.f;
+  if (cudaEventRecord(e0, st) == cudaSuccess && batch_enqueue(b, st) == EIC_OK &&
+      cudaEventRecord(e1, st) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess &&
+      cudaEventElapsedTime(&t, e0, e1) == cudaSuccess && batch_wait(b, st, nullptr) == EIC_OK)
+    ms = t;
+  (void)cudaGetLastError();
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return ms;
+}
+
+}  // namespace
+
+extern "C" {
+
 int eic_sssp_batch(const eic_graph* const* graphs, const uint32_t* sources, uint32_t num_queries,
                    uint32_t* const* dists, const eic_params* params, int* statuses, void* stream) {
   if (num_queries == 0) return EIC_OK;
   if (!graphs || !sources || !dists) return EIC_EINVAL;
-  eic_params p;
-  int rc = resolve_params(params, &p);
-  if (rc) return rc;
-  for (uint32_t i = 0; i < num_queries; ++i) {
-    if (!graphs[i] || !dists[i] || sources[i] >= graphs[i]->dg.n) {
-      if (statuses)
-        for (uint32_t j = 0; j < num_queries; ++j) statuses[j] = EIC_EINVAL;
-      return EIC_EINVAL;
-    }
+  if (!graphs[0]) return EIC_EINVAL;
+  DeviceGuard guard(graphs[0]->device);
+  if (!guard.ok || graphs[0]->device < 0 || graphs[0]->device >= kMaxDevices) return EIC_ECUDA;
+  std::lock_guard<std::mutex> lock(g_pool_mu);
+  eic_batch* b = nullptr;
+  int rc = batch_create(graphs, sources, num_queries, dists, params, &g_pool[graphs[0]->device], &b);
+  if (rc) {
+    if (statuses)
+      for (uint32_t i = 0; i < num_queries; ++i) statuses[i] = rc;
+    return rc;
   }
+  b->use_graph = false;  // one-shot: launch directly
   cudaStream_t st = (cudaStream_t)stream;
-  std::lock_guard<std::mutex> block(g_batch_mu);
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+  rc = batch_enqueue(b, st);
+  if (rc == EIC_OK) {
+    rc = batch_wait(b, st, statuses);
+  } else {
+    cudaStreamSynchronize(st);
     (void)cudaGetLastError();
-    return EIC_ECUDA;
+    if (statuses)
+      for (uint32_t i = 0; i < num_queries; ++i) statuses[i] = rc;
   }
-  BatchBuffers& bb = g_batch[dev];
-  if (bb.cap < num_queries) {
-    cudaFree(bb.dstat);
-    if (bb.hstat) cudaFreeHost(bb.hstat);
-    bb.dstat = nullptr;
-    bb.hstat = nullptr;
-    bb.cap = 0;
-    if (cudaMalloc((void**)&bb.dstat, num_queries * sizeof(int)) != cudaSuccess ||
-        cudaMallocHost((void**)&bb.hstat, num_queries * sizeof(int)) != cudaSuccess) {
-      (void)cudaGetLastError();
-      return EIC_ENOMEM;
+  batch_free(b);
+  return rc;
+}
+
+int eic_batch_create(const eic_graph* const* graphs, const uint32_t* sources, uint32_t num_queries,
+                     uint32_t* const* dists, const eic_params* params, eic_batch** out) {
+  if (!out) return EIC_EINVAL;
+  *out = nullptr;
+  if (!graphs || !graphs[0]) return EIC_EINVAL;
+  DeviceGuard guard(graphs[0]->device);
+  if (!guard.ok) return EIC_ECUDA;
+  return batch_create(graphs, sources, num_queries, dists, params, nullptr, out);
+}
+
+int eic_batch_run(eic_batch* b, void* stream) {
+  if (!b) return EIC_EINVAL;
+  DeviceGuard guard(b->device);
+  if (!guard.ok) return EIC_ECUDA;
+  return batch_run(b, (cudaStream_t)stream);
+}
+
+int eic_batch_wait(eic_batch* b, void* stream, int* statuses) {
+  if (!b) return EIC_EINVAL;
+  DeviceGuard guard(b->device);
+  if (!guard.ok) return EIC_ECUDA;
+  return batch_wait(b, (cudaStream_t)stream, statuses);
+}
+
+int eic_batch_tune(eic_batch* b, void* stream, eic_batch_config* best) {
+  if (!b) return EIC_EINVAL;
+  DeviceGuard guard(b->device);
+  if (!guard.ok) return EIC_ECUDA;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (!b->hq.empty()) {
+    const uint32_t nrun = (uint32_t)b->hq.size();
+    uint32_t best_g = b->groups, best_block = b->block;
+    eic_params best_p = b->p;
+    double best_ms = 1e300;
+    // one configuration: a warm-up run, then a timed one when the warm-up was
+    // within 2x of the best so far; returns the time (or < 0 on error)
+    auto trial = [&](uint32_t g, uint32_t block, const eic_params& pp, double* ms_out) -> int {
+      b->p = pp;
+      int rc = batch_configure(b, g, block);
+      if (rc) return rc;
+      double ms = batch_time(b, st);
+      if (ms < 0) return EIC_ECUDA;
+      if (ms < 2.0 * best_ms) {
+        const double ms2 = batch_time(b, st);
+        if (ms2 < 0) return EIC_ECUDA;
+        ms = ms2 < ms ? ms2 : ms;
+      }
+      if (ms < best_ms) {
+        best_ms = ms;
+        best_g = b->groups;
+        best_block = b->block;
+        best_p = pp;
+      }
+      if (ms_out) *ms_out = ms;
+      return EIC_OK;
+    };
+    uint32_t gmax = 0;
+    int rc = batch_grid((int)b->block, &gmax);
+    if (rc) return rc;
+    // pass 1: group counts (divisors of the grid and powers of two), from the
+    // most groups down, until two in a row are 20% slower than the best
+    std::vector<uint32_t> cand;
+    for (uint32_t g = gmax; g >= 1; --g)
+      if (g <= nrun && (gmax % g == 0 || (g & (g - 1)) == 0)) cand.push_back(g);
+    uint32_t worse = 0;
+    const eic_params base = b->p;
+    for (uint32_t g : cand) {
+      double ms = 0;
+      if ((rc = trial(g, b->block, base, &ms))) return rc;
+      worse = ms > 1.2 * best_ms ? worse + 1 : 0;
+      if (worse >= 2) break;
     }
-    bb.cap = num_queries;
-  }
-  int* dstat = bb.dstat;
-  int* hstat = bb.hstat;
-  cudaMemsetAsync(dstat, 0, num_queries * sizeof(int), st);
-  int first_err = EIC_OK;
-  for (uint32_t i = 0; i < num_queries && first_err == EIC_OK; ++i) {
-    eic_graph* g = const_cast<eic_graph*>(graphs[i]);
-    std::lock_guard<std::mutex> lock(g->mu);
-    DeviceGuard dg(g->device);
-    if (g->dg.two_m == 0) {
-      if ((rc = trivial_query(g, sources[i], dists[i], nullptr, st))) first_err = rc;
-      continue;
+    // pass 2 at the best group count: step-width scaling upwards while it
+    // helps, then the window-class threshold, then a 256-thread block
+    for (uint32_t gs = best_p.gap_shift + 1; gs <= 8; ++gs) {
+      eic_params pp = best_p;
+      pp.gap_shift = gs;
+      const double before = best_ms;
+      if ((rc = trial(best_g, best_block, pp, nullptr))) return rc;
+      if (best_ms >= before) break;
     }
-    if ((rc = eic_ws_ensure(g, 0)) || (rc = enqueue_query(g, sources[i], dists[i], nullptr, p, dstat + i, st)))
-      first_err = rc;
+    for (uint32_t hm : {64u, 256u}) {
+      eic_params pp = best_p;
+      pp.heavy_min = hm;
+      if ((rc = trial(best_g, best_block, pp, nullptr))) return rc;
+    }
+    if ((rc = trial(best_g, 256, best_p, nullptr))) return rc;
+    // keep the winner; the scratch shrinks to its group count
+    b->p = best_p;
+    if (b->pool == &b->own && b->own.count > best_g) b->own.release();
+    if ((rc = batch_configure(b, best_g, best_block))) return rc;
+    if (b->exec) {
+      cudaGraphExecDestroy(b->exec);
+      b->exec = nullptr;
+    }
+    b->tuned_ms = best_ms;
   }
-  if (cudaMemcpyAsync(hstat, dstat, num_queries * sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-      cudaStreamSynchronize(st) != cudaSuccess) {
-    (void)cudaGetLastError();
-    if (first_err == EIC_OK) first_err = EIC_ECUDA;
-  }
-  for (uint32_t i = 0; i < num_queries; ++i) {
-    int s_i = first_err != EIC_OK ? first_err : hstat[i];
-    if (statuses) statuses[i] = s_i;
-    if (first_err == EIC_OK && s_i != EIC_OK) first_err = s_i;
-  }
-  return first_err;
+  return best ? eic_batch_info(b, best) : EIC_OK;
+}
+
+int eic_batch_info(const eic_batch* b, eic_batch_config* out) {
+  if (!b || !out) return EIC_EINVAL;
+  memset(out, 0, sizeof(*out));
+  out->groups = b->groups;
+  out->blocks_per_group = b->nb;
+  out->block_threads = b->block;
+  out->cuda_graph = b->exec ? 1u : 0u;
+  out->gap_shift = b->p.gap_shift;
+  out->heavy_min = b->p.heavy_min;
+  out->queries = b->nq;
+  out->scratch_bytes = (uint64_t)b->pool->count * b->pool->slot_bytes;
+  out->tuned_ms = b->tuned_ms;
+  return EIC_OK;
+}
+
+int eic_batch_destroy(eic_batch* b) {
+  if (!b) return EIC_OK;
+  DeviceGuard guard(b->device);
+  batch_free(b);
+  return EIC_OK;
 }
 
 }  // extern "C"
+
 
 // ------------------------------------------------ allocation-free entry point
 //
@@ -1582,6 +2270,7 @@ extern "C" int eic_sssp_noalloc(const eic_graph* gc, uint32_t source, uint32_t* 
   A.trace_cap = 0;
   A.timeline = nullptr;
   A.timeline_cap = 0;
+  A.nb = (uint32_t)nd.grid;
   EIC_CUDA_TRY(cudaMemsetAsync(A.dist, 0xFF, (uint64_t)G.ni * 4, st));
   EIC_CUDA_TRY(cudaMemsetAsync(A.sbits, 0, ((uint64_t)G.ni / 32 + 2) * 4, st));
   EIC_CUDA_TRY(cudaMemsetAsync(A.fbits, 0, 2 * ((uint64_t)G.ni / 32 + 2) * 4, st));

@@ -41,8 +41,9 @@ def test_host_only_calls(lib):
     p = binding.default_params()
     assert (p.alpha, p.beta, p.st_num, p.gap_shift, p.flags) == (3, 0.9, 1024, 0, 0)
     assert lib.eic_params_default(None) == binding.EINVAL
-    for code in range(8):
-        assert lib.eic_strerror(code)
+    for code in range(9):
+        assert lib.eic_strerror(code) and lib.eic_strerror(code) != b"unknown status"
+    assert lib.eic_strerror(99) == b"unknown status"
     assert lib.eic_version() >= 100
     out = ctypes.c_void_p()
     # argument checks happen before any device call
@@ -53,3 +54,55 @@ def test_host_only_calls(lib):
     assert lib.eic_graph_destroy(None) == binding.OK
     assert lib.eic_sssp(None, 0, None, None, None, None, None) == binding.EINVAL
     assert lib.eic_sssp_batch(None, None, 0, None, None, None, None) == binding.OK
+    assert lib.eic_sssp_batch(None, None, 3, None, None, None, None) == binding.EINVAL
+    assert lib.eic_batch_create(None, None, 1, None, None, None) == binding.EINVAL
+    assert lib.eic_batch_create(None, None, 1, None, None, ctypes.byref(out)) == binding.EINVAL
+    assert lib.eic_batch_run(None, None) == binding.EINVAL
+    assert lib.eic_batch_wait(None, None, None) == binding.EINVAL
+    assert lib.eic_batch_tune(None, None, None) == binding.EINVAL
+    assert lib.eic_batch_info(None, None) == binding.EINVAL
+    assert lib.eic_batch_destroy(None) == binding.OK
+
+
+def test_struct_layouts_match_the_header():
+    from paper_2506_19349_gb300 import binding
+
+    # eic_params: u32, (pad), f64, 6 x u32, batch_groups, reserved[7]
+    assert ctypes.sizeof(binding.Params) == 4 + 4 + 8 + 6 * 4 + 4 + 7 * 4
+    assert binding.Params.batch_groups.offset == 40
+    # eic_batch_config: 8 x u32, u64, f64
+    assert ctypes.sizeof(binding.BatchConfig) == 8 * 4 + 8 + 8
+
+
+def test_ctypes_mirrors_match_the_c_layout(tmp_path):
+    """sizeof/offsetof of the header's structs, compiled by the C compiler,
+    equal the binding's ctypes mirrors."""
+    import shutil
+    import subprocess
+
+    from paper_2506_19349_gb300 import binding
+
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    checks = {"eic_params": (binding.Params, ["beta", "st_num", "flags", "batch_groups", "reserved"]),
+              "eic_step": (binding.Step, ["lb", "ub", "st", "gap_lb", "sumd_lb", "highd_lb", "rounds", "settled"]),
+              "eic_stats": (binding.Stats, ["steps", "pull_items", "trace", "trace_cap", "trace_len", "timeline",
+                                            "timeline_cap", "timeline_len", "kernel_ms"]),
+              "eic_batch_config": (binding.BatchConfig, ["groups", "queries", "scratch_bytes", "tuned_ms"])}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "eic.h"', "int main(void) {"]
+    for st, (_, fields) in checks.items():
+        lines.append(f'  printf("{st} %zu\\n", sizeof({st}));')
+        for f in fields:
+            lines.append(f'  printf("{st}.{f} %zu\\n", offsetof({st}, {f}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = dict(line.split() for line in subprocess.run([str(exe)], check=True, capture_output=True,
+                                                        text=True).stdout.splitlines())
+    for st, (cls, fields) in checks.items():
+        assert int(got[st]) == ctypes.sizeof(cls), st
+        for f in fields:
+            assert int(got[f"{st}.{f}"]) == getattr(cls, f).offset, f"{st}.{f}"
