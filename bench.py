@@ -139,10 +139,41 @@ class ClockSampler:
         return out
 
 
-def make_workload(scale: int, nsources: int):
+def make_workload(scale: int, nsources: int, rank: int = 0):
+    """The resident graph (the same on every rank) and this rank's sources
+    (replicas draw their own, so N ranks process N x nsources queries)."""
     from paper_2506_19349_gb300 import graphgen
 
-    return graphgen.kron(scale, seed=2, nsources=nsources)
+    return graphgen.kron(scale, seed=2, nsources=nsources, source_seed=2 + 1000 * rank)
+
+
+def max_over_ranks(x: float, world: int, device) -> float:
+    """Largest value over the ranks (the job's time is its slowest rank's)."""
+    if world == 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(x: float, world: int, device) -> float:
+    """Sum over the ranks (units every rank processed)."""
+    if world == 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def whole_job_gteps(edges_all_ranks_per_step: float, steps: int, max_ms: float) -> float:
+    """Edges of all ranks' queries over the slowest rank's time, in GTEPS."""
+    return edges_all_ranks_per_step * steps / (max_ms * 1e-3) / 1e9
 
 
 def workload_config(wl, scale, nsources):
@@ -343,7 +374,7 @@ def main():
     import paper_2506_19349_gb300 as eic
 
     t0 = time.perf_counter()
-    wl = make_workload(args.scale, args.sources)
+    wl = make_workload(args.scale, args.sources, rank)
     gen_s = time.perf_counter() - t0
     stream = torch.cuda.current_stream()
     torch.cuda.synchronize()
@@ -406,12 +437,10 @@ def main():
     clocks = sampler.stop()
     total_ms = start.elapsed_time(end)
     q_ms = [a.elapsed_time(b) for evs in per_query for a, b in evs]
-    if world > 1:
-        t = torch.tensor([total_ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(total_ms, world, "cuda")
+    edges_all_ranks = sum_over_ranks(edges_per_step, world, "cuda")
     ms_per_step = total_ms / args.steps
-    value = world * edges_per_step * args.steps / (total_ms * 1e-3) / 1e9
+    value = whole_job_gteps(edges_all_ranks, args.steps, total_ms)
 
     # roofline of the query kernel: algorithmic bytes per launch over its event duration
     b_alg = [16 * inf["frontier"] + 12 * inf["traversed"] + 8 * inf["improved"] + 12 * inf["pull_items"] + 4 * n
@@ -440,16 +469,12 @@ def main():
                 host_out[i & 1].copy_(dists[i], non_blocking=True)
         e_end.record(stream)
         torch.cuda.synchronize()
-        e2e_ms = e_start.elapsed_time(e_end)
-        if world > 1:
-            t = torch.tensor([e2e_ms], device="cuda")
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            e2e_ms = float(t.item())
-        e2e = {"value": world * edges_per_step * args.steps / (e2e_ms * 1e-3) / 1e9, "unit": "GTEPS",
+        e2e_ms = max_over_ranks(e_start.elapsed_time(e_end), world, "cuda")
+        e2e = {"value": whole_job_gteps(edges_all_ranks, args.steps, e2e_ms), "unit": "GTEPS",
                "h2d_bytes_per_step": 4 * q, "d2h_bytes_per_step": 4 * n * q}
 
     batched = None
-    if not args.no_batched:
+    if not args.no_batched and world == 1:
         batched = {"same_workload": batched_same_workload(eic, torch, g, srcs, dists, stream, max(args.steps, 1),
                                                           value / world, edges_per_step)}
         del g, dists, deg

@@ -62,6 +62,16 @@ def _load():
             lib.gg_weights_uniform.restype = None
             lib.gg_weights_uniform.argtypes = [ctypes.c_uint64, u32p, u32p, ctypes.c_uint64, ctypes.c_uint32,
                                                ctypes.c_uint32, u32p, ctypes.c_int]
+            lib.gg_weights_discretize.restype = None
+            lib.gg_weights_discretize.argtypes = [ctypes.c_uint64, u32p, u32p, ctypes.c_uint64, ctypes.c_uint32,
+                                                  u32p, ctypes.c_int]
+            lib.gg_weights_converge.restype = None
+            lib.gg_weights_converge.argtypes = [ctypes.c_uint64, u32p, u32p, ctypes.c_uint64, ctypes.c_double,
+                                                u32p, ctypes.c_int]
+            lib.gg_discretize_value.restype = ctypes.c_uint32
+            lib.gg_discretize_value.argtypes = [ctypes.c_double, ctypes.c_uint32]
+            lib.gg_converge_value.restype = ctypes.c_double
+            lib.gg_converge_value.argtypes = [ctypes.c_double, ctypes.c_double]
             lib.gg_weights_lognormal.restype = None
             lib.gg_weights_lognormal.argtypes = [ctypes.c_uint64, u32p, u32p, ctypes.c_uint64, ctypes.c_double,
                                                  ctypes.c_double, ctypes.c_uint32, ctypes.c_uint32, u32p,
@@ -137,6 +147,34 @@ def weights_uniform(src, dst, seed: int, wmin: int, wmax: int, out=None) -> np.n
     return w
 
 
+def weights_discretize(src, dst, seed: int, power: int, out=None) -> np.ndarray:
+    """The paper's power variant (Eq. 7): 1 + round(x (2^power - 2)), x uniform in (0,1] per pair."""
+    if not 1 <= power <= 31:
+        raise ValueError("power must be in 1..31")
+    w = out if out is not None else np.empty(src.size, dtype=np.uint32)
+    _load().gg_weights_discretize(src.size, _ptr(src), _ptr(dst), seed, power, _ptr(w), _threads())
+    return w
+
+
+def weights_converge(src, dst, seed: int, pivot: float, out=None) -> np.ndarray:
+    """The paper's pivot variant (Eq. 8), quantised to 1..65535 by Eq. 7 with power 16."""
+    if not 0.0 < pivot < 1.0:
+        raise ValueError("pivot must be in (0, 1)")
+    w = out if out is not None else np.empty(src.size, dtype=np.uint32)
+    _load().gg_weights_converge(src.size, _ptr(src), _ptr(dst), seed, pivot, _ptr(w), _threads())
+    return w
+
+
+def discretize(x: float, power: int) -> int:
+    """Eq. 7 on one value, rounded to the nearest integer (halves up)."""
+    return int(_load().gg_discretize_value(x, power))
+
+
+def converge(x: float, pivot: float) -> float:
+    """Eq. 8 on one value."""
+    return float(_load().gg_converge_value(x, pivot))
+
+
 def weights_lognormal(src, dst, seed: int, mu: float, sigma: float, wmin: int, wmax: int, out=None) -> np.ndarray:
     w = _out(src.size, out)
     _load().gg_weights_lognormal(src.size, _ptr(src), _ptr(dst), seed, mu, sigma, wmin, wmax, _ptr(w), _threads())
@@ -175,7 +213,9 @@ def kron(scale: int, seed: int = 2, edgefactor: int = 16, weights: str = "unifor
     """RMAT scale/edgefactor graph, ids permuted, weights per unordered pair.
 
     weights: "uniform255" -> integers uniform in [1,255];
-             "lognormal"  -> clamp(llround(exp(3 + 1.5 Z)), 1, 65535).
+             "lognormal"  -> clamp(llround(exp(3 + 1.5 Z)), 1, 65535);
+             "power:P"    -> the paper's power variant, Eq. 7 with power P;
+             "pivot:Y"    -> the paper's pivot variant, Eq. 8 with pivot Y, as integers 1..65535.
     Sources: uniform over vertices with at least one non-loop edge.
     """
     ne = edgefactor << scale
@@ -185,6 +225,10 @@ def kron(scale: int, seed: int = 2, edgefactor: int = 16, weights: str = "unifor
         w = weights_uniform(src, dst, seed, 1, 255, out=o.get("w"))
     elif weights == "lognormal":
         w = weights_lognormal(src, dst, seed, 3.0, 1.5, 1, 65535, out=o.get("w"))
+    elif weights.startswith("power:"):
+        w = weights_discretize(src, dst, seed, int(weights[6:]), out=o.get("w"))
+    elif weights.startswith("pivot:"):
+        w = weights_converge(src, dst, seed, float(weights[6:]), out=o.get("w"))
     else:
         raise ValueError(weights)
     ss = seed if source_seed is None else source_seed

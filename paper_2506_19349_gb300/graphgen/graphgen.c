@@ -16,8 +16,9 @@
  * GAPBS Kron-like, a,b,c,d = 0.57,0.19,0.19,0.05), and a perturbed grid that
  * stands in for the Road graph. Weights are integers; the paper's real-valued
  * weights in (0,1] are replaced by uniform integers (or a clamped log-normal
- * for the heavy-tailed variant), and the weight of an undirected pair is a
- * hash of the pair, so duplicates and both directions always agree.
+ * for the heavy-tailed variant, or the paper's power and pivot variants of
+ * Eq. 7-8), and the weight of an undirected pair is a hash of the pair, so
+ * duplicates and both directions always agree.
  */
 #include <math.h>
 #include <pthread.h>
@@ -265,8 +266,29 @@ typedef struct {
   uint64_t seed;
   uint32_t wmin, wmax;
   double mu, sigma;
-  int kind;
+  int kind;  /* 0 uniform, 1 log-normal, 2 discretize(x, power), 3 converge(x, pivot) */
+  uint32_t power;
+  double pivot;
 } gg_w_ctx;
+
+/* The benchmark graphs' weight x, uniform in (0,1], per unordered pair. */
+static inline double gg_unit_weight(uint64_t seed, uint64_t key) { return 1.0 - gg_unit(gg_rand(seed, 10, key)); }
+
+/* Eq. 7: discretize(x, y) = 1 + x (2^y - 2), rounded to the nearest integer
+ * (halves up): the 2^y - 1 integers 1 .. 2^y - 1 for x in (0, 1]. */
+static inline uint32_t gg_discretize(double x, uint32_t y) {
+  const double span = (double)((1ull << y) - 2);
+  uint64_t q = (uint64_t)floor(x * span + 0.5);
+  if (q > (1ull << y) - 2) q = (1ull << y) - 2;
+  return (uint32_t)(1 + q);
+}
+
+/* Eq. 8: converge(x, y), a bell-shaped weight in [0, 1] with its peak and
+ * median at the pivot y. */
+static inline double gg_converge(double x, double y) {
+  const double t = (1.0 - 2.0 * x) * (1.0 - 2.0 * x);
+  return x <= 0.5 ? y - y * t : y + (1.0 - y) * t;
+}
 
 static inline uint64_t gg_pair_key(uint32_t u, uint32_t v) {
   return u < v ? ((uint64_t)u << 32) | v : ((uint64_t)v << 32) | u;
@@ -279,6 +301,10 @@ static void gg_w_range(void* p, uint64_t lo, uint64_t hi) {
     uint64_t key = gg_pair_key(c->src[e], c->dst[e]);
     if (c->kind == 0) {
       c->w[e] = c->wmin + gg_below(gg_rand(c->seed, 7, key), range);
+    } else if (c->kind == 2) {
+      c->w[e] = gg_discretize(gg_unit_weight(c->seed, key), c->power);
+    } else if (c->kind == 3) {  /* the real weight quantised to 1..65535 by discretize(., 16) */
+      c->w[e] = gg_discretize(gg_converge(gg_unit_weight(c->seed, key), c->pivot), 16);
     } else {
       double u1 = gg_unit(gg_rand(c->seed, 8, key));
       double u2 = gg_unit(gg_rand(c->seed, 9, key));
@@ -296,7 +322,7 @@ static void gg_w_range(void* p, uint64_t lo, uint64_t hi) {
 /* Integer weight uniform in [wmin, wmax], a function of the unordered pair. */
 void gg_weights_uniform(uint64_t ne, const uint32_t* src, const uint32_t* dst, uint64_t seed, uint32_t wmin,
                         uint32_t wmax, uint32_t* w, int nthreads) {
-  gg_w_ctx c = {src, dst, w, seed, wmin, wmax, 0.0, 0.0, 0};
+  gg_w_ctx c = {src, dst, w, seed, wmin, wmax, 0.0, 0.0, 0, 0, 0.0};
   gg_parallel(ne, nthreads, gg_w_range, &c);
 }
 
@@ -304,9 +330,30 @@ void gg_weights_uniform(uint64_t ne, const uint32_t* src, const uint32_t* dst, u
  * Box-Muller transform, a function of the unordered pair. */
 void gg_weights_lognormal(uint64_t ne, const uint32_t* src, const uint32_t* dst, uint64_t seed, double mu,
                           double sigma, uint32_t wmin, uint32_t wmax, uint32_t* w, int nthreads) {
-  gg_w_ctx c = {src, dst, w, seed, wmin, wmax, mu, sigma, 1};
+  gg_w_ctx c = {src, dst, w, seed, wmin, wmax, mu, sigma, 1, 0, 0.0};
   gg_parallel(ne, nthreads, gg_w_range, &c);
 }
+
+/* The paper's power variants (Section 4.2): discretize(x, power) of Eq. 7,
+ * rounded, with x uniform in (0,1] per unordered pair; power in 1..31. */
+void gg_weights_discretize(uint64_t ne, const uint32_t* src, const uint32_t* dst, uint64_t seed, uint32_t power,
+                           uint32_t* w, int nthreads) {
+  gg_w_ctx c = {src, dst, w, seed, 1, 0, 0.0, 0.0, 2, power, 0.0};
+  gg_parallel(ne, nthreads, gg_w_range, &c);
+}
+
+/* The paper's pivot variants (Section 4.2): converge(x, pivot) of Eq. 8 with x
+ * uniform in (0,1] per unordered pair, then discretize(., 16) to integers
+ * 1..65535 (the path takes integer weights). */
+void gg_weights_converge(uint64_t ne, const uint32_t* src, const uint32_t* dst, uint64_t seed, double pivot,
+                         uint32_t* w, int nthreads) {
+  gg_w_ctx c = {src, dst, w, seed, 1, 0, 0.0, 0.0, 3, 0, pivot};
+  gg_parallel(ne, nthreads, gg_w_range, &c);
+}
+
+/* Eq. 7 and Eq. 8 on single values (for tests of the transforms). */
+uint32_t gg_discretize_value(double x, uint32_t power) { return gg_discretize(x, power); }
+double gg_converge_value(double x, double pivot) { return gg_converge(x, pivot); }
 
 /* ------------------------------------------------------------- sources */
 

@@ -49,6 +49,11 @@ def _cases():
     w = G.kron(12, seed=26, nsources=3)
     w.w = (w.w % 3 + 1).astype(np.uint32)
     yield "kron12_w123", w
+    # the paper's weight variants (Eq. 7 power, Eq. 8 pivot)
+    for p in (1, 4, 10):
+        yield f"kron12_power{p}", G.kron(12, seed=27, weights=f"power:{p}", nsources=2)
+    for y in (0.1, 0.9):
+        yield f"kron12_pivot{y}", G.kron(12, seed=28, weights=f"pivot:{y}", nsources=2)
 
 
 CASES = list(_cases())
