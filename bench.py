@@ -53,6 +53,7 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched measurements")
+    ap.add_argument("--no-served", action="store_true", help="skip the serving measurement")
     return ap.parse_args()
 
 
@@ -351,6 +352,108 @@ def batched_mixed(eic, torch, stream, runs):
             "speedup": gteps / plain_gteps}
 
 
+def serving(eic, torch, stream, rates, seconds_per_rate, max_per_rate):
+    """Resident set of 8 graphs (RMAT scales 18..23, a second scale-22 seed, a
+    2048^2 grid), Poisson request streams at each rate through eic_server_*;
+    against one-at-a-time plain solves of the same requests (their measured
+    service times replayed in arrival order)."""
+    import numpy as np
+    from paper_2506_19349_gb300 import graphgen
+
+    t0 = time.perf_counter()
+    wls = [graphgen.kron(s, seed=200 + s, nsources=1) for s in (18, 19, 20, 21, 22, 23)]
+    wls.append(graphgen.kron(22, seed=300, nsources=1))
+    wls.append(graphgen.road(2048, seed=301, wmax=255, nsources=1))
+    gen_s = time.perf_counter() - t0
+    graphs = [eic.Graph(w.n, w.src, w.dst, w.w) for w in wls]
+    pools = [graphgen.pick_sources(w.n, w.src, w.dst, 32, 400 + k, "nonisolated") for k, w in enumerate(wls)]
+    del wls
+    # the request pool: 32 sources per graph; plain service time of each, on the device
+    pool = [(g, int(s)) for g in range(len(graphs)) for s in pools[g]]
+    dist = {g: eic.new_dist(graphs[g].n) for g in range(len(graphs))}
+    svc = []
+    for g, s in pool[:: len(pool) // 16]:  # warm-up
+        eic.sssp(graphs[g], s, dist=dist[g])
+    for g, s in pool:
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        eic.sssp(graphs[g], s, dist=dist[g])
+        e1.record(stream)
+        e1.synchronize()
+        svc.append(e0.elapsed_time(e1))
+    plain_qps = 1000.0 / statistics.mean(svc)
+    del dist
+    srv = eic.Server(graphs)
+    rows = []
+    rng = np.random.default_rng(11)
+    switch = sys.getswitchinterval()
+    sys.setswitchinterval(1e-4)  # the consumer thread releases results promptly
+    for rate in rates:
+        n_req = int(min(max_per_rate, max(50, rate * seconds_per_rate)))
+        picks = rng.integers(len(pool), size=n_req)
+        gaps = rng.exponential(1.0 / rate, size=n_req) if rate != float("inf") else np.zeros(n_req)
+        arrive = np.cumsum(gaps)
+        srv.reset_stats()
+        tickets = []
+        done_lat = []
+
+        def consume():
+            k = 0
+            while k < n_req:
+                if k >= len(tickets):
+                    time.sleep(0.0002)
+                    continue
+                t = tickets[k]
+                st = srv.wait(t, 600000)
+                if st != 0:
+                    raise RuntimeError(f"request status {st}")
+                _, lat = srv.result(t, to_host=False)
+                done_lat.append(lat)
+                srv.release(t)
+                k += 1
+
+        th = threading.Thread(target=consume)
+        th.start()
+        start = time.perf_counter()
+        for k in range(n_req):
+            ahead = arrive[k] - (time.perf_counter() - start)
+            if ahead > 3e-4:  # sleep (releasing the interpreter lock) until close to the arrival
+                time.sleep(ahead - 2e-4)
+            while time.perf_counter() - start < arrive[k]:
+                pass
+            g, s = pool[picks[k]]
+            tickets.append(srv.submit(g, s))
+        th.join()
+        wall = time.perf_counter() - start
+        st = srv.stats()
+        # one at a time: request k starts when it has arrived and k-1 is done
+        fin, lat1 = 0.0, []
+        for k in range(n_req):
+            begin = max(arrive[k] * 1e3, fin)
+            fin = begin + svc[picks[k]]
+            lat1.append(fin - arrive[k] * 1e3)
+        lat1.sort()
+        dl = sorted(done_lat)
+        rows.append({"rate_per_s": rate if rate != float("inf") else "all at once", "requests": n_req,
+                     "served": {"qps": n_req / wall, "p50_ms": dl[len(dl) // 2],
+                                "p99_ms": dl[min(len(dl) - 1, int(0.99 * len(dl)))],
+                                "max_in_flight": st["max_in_flight"], "kernel_launches": st["kernel_launches"]},
+                     "one_at_a_time": {"qps": n_req / (fin * 1e-3), "p50_ms": lat1[len(lat1) // 2],
+                                       "p99_ms": lat1[min(len(lat1) - 1, int(0.99 * len(lat1)))]}})
+    sys.setswitchinterval(switch)
+    info = srv.stats()
+    srv.close()
+    best = max(r["served"]["qps"] for r in rows)
+    return {"workload": "resident RMAT scales 18,19,20,21,22,22,23 and a 2048^2 grid (weights [1,255]); requests "
+                        "(graph, source) uniform over 32 sources per graph, Poisson arrivals",
+            "generate_s": gen_s, "groups": info["groups"], "blocks_per_group": info["blocks_per_group"],
+            "plain_one_at_a_time_qps": plain_qps, "plain_service_ms_mean": statistics.mean(svc),
+            "rates": rows, "peak_served_qps": best, "speedup_vs_one_at_a_time": best / plain_qps,
+            "latency": "submit to completion seen by the host runtime; one-at-a-time latencies replay the measured "
+                       "plain service times of the same requests in arrival order"}
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
@@ -480,6 +583,10 @@ def main():
         del g, dists, deg
         torch.cuda.empty_cache()
         batched["mixed_32_graphs"] = batched_mixed(eic, torch, stream, max(args.steps, 1))
+    served = None
+    if not args.no_served and world == 1:
+        torch.cuda.empty_cache()
+        served = serving(eic, torch, stream, (100, 1000, 5000, 20000, float("inf")), 1.0, 2000)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -511,6 +618,7 @@ def main():
                               for k in ("steps", "rounds", "frontier", "traversed", "pulls", "improved", "heavy",
                                         "pull_items")},
             "batched": batched,
+            "served": served,
         }
         print(json.dumps(line), flush=True)
     if world > 1:

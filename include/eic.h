@@ -269,6 +269,77 @@ int eic_batch_info(const eic_batch* b, eic_batch_config* out);
 int eic_batch_destroy(eic_batch* b);
 
 /*
+ * Serving: a request loop with continuous batching (no counterpart in the
+ * paper). Graphs stay resident; (graph, source) requests are submitted at any
+ * time and run as soon as a block group of the persistent serving kernel is
+ * free, while other requests are in flight. Results are exact and identical
+ * to eic_sssp's.
+ *
+ * Admission: requests are admitted in arrival order while the result-buffer
+ * budget (config.output_bytes, a device arena allocated at creation; a result
+ * takes 4n bytes, rounded up to 256) and the request ring (config.
+ * ring_entries in flight) have room; the rest wait in a host queue. A result's
+ * memory returns to the budget at eic_server_release. The serving kernel runs
+ * while there is work: after config.idle_us without a request, once no
+ * request runs, a block group registers as idle, and when every group is
+ * registered they leave together; the runtime relaunches the kernel when
+ * requests arrive again. Scratch: one slot per group sized for the largest
+ * resident graph (as a batch's).
+ *
+ * eic_server_create   graphs (host array of num_graphs, all on one device)
+ *                     stay owned by the caller and must outlive the server;
+ *                     params as eic_sssp's (NULL = defaults); config may be
+ *                     NULL. Starts the runtime's pump thread. Errors:
+ *                     EIC_EINVAL, EIC_ENOMEM, EIC_ECUDA.
+ * eic_server_submit   enqueues (graph index, source); *ticket identifies it.
+ *                     Never blocks. EIC_EINVAL for a bad index or source,
+ *                     EIC_ENOMEM if the result cannot fit the whole budget.
+ * eic_server_poll     EIC_OK and *status once done; EIC_EBUSY while pending.
+ * eic_server_wait     waits up to timeout_ms: EIC_OK and *status once done,
+ *                     EIC_ETIMEOUT if still pending.
+ * eic_server_result   for a done request: copies the n distances to
+ *                     host_dist (if non-NULL), returns the device buffer in
+ *                     *device_dist (if non-NULL; valid until release) and the
+ *                     latency from submit to completion in *latency_ms. Returns
+ *                     the request's status (EIC_EBUSY while pending).
+ * eic_server_release  forgets a done request and frees its result buffer.
+ * eic_server_stats    counters and the latency percentiles of the requests
+ *                     completed since creation or the last reset.
+ * eic_server_destroy  stops the kernel and the pump; pending requests are
+ *                     dropped. NULL accepted.
+ */
+typedef struct eic_server eic_server;
+
+typedef struct {
+  uint32_t groups;        /* block groups serving at the same time (0 = about 8 blocks per group) */
+  uint32_t ring_entries;  /* admitted requests in flight at most, a power of two (0 = 1024) */
+  uint64_t output_bytes;  /* device budget for result buffers (0 = 64 results of the largest graph) */
+  uint32_t idle_us;       /* idle time before a block group registers as idle (0 = 2000, at most 100000) */
+  uint32_t reserved[5];
+} eic_server_config;
+
+typedef struct {
+  uint64_t submitted, admitted, completed, queued, in_flight, max_in_flight;
+  uint64_t kernel_launches;
+  uint64_t output_bytes_used, output_bytes, scratch_bytes;
+  uint32_t groups, blocks_per_group;
+  double latency_p50_ms, latency_p99_ms, latency_mean_ms;  /* submit to completion */
+  uint64_t latency_count;
+} eic_server_report;
+
+int eic_server_create(const eic_graph* const* graphs, uint32_t num_graphs, const eic_params* params,
+                      const eic_server_config* config, eic_server** out);
+int eic_server_submit(eic_server* s, uint32_t graph, uint32_t source, uint64_t* ticket);
+int eic_server_poll(eic_server* s, uint64_t ticket, int* status);
+int eic_server_wait(eic_server* s, uint64_t ticket, uint32_t timeout_ms, int* status);
+int eic_server_result(eic_server* s, uint64_t ticket, uint32_t* host_dist, const uint32_t** device_dist,
+                      double* latency_ms);
+int eic_server_release(eic_server* s, uint64_t ticket);
+int eic_server_stats(eic_server* s, eic_server_report* out);
+int eic_server_reset_stats(eic_server* s);
+int eic_server_destroy(eic_server* s);
+
+/*
  * Allocation-free single-source query. The paper has no counterpart: this
  * entry point exists for callers that cannot call cudaMalloc at query time,
  * for example a serving process that plans its whole device-memory budget up

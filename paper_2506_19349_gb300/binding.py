@@ -26,7 +26,9 @@ FLAG_NO_PULL = 1
 EXPORTS = ("eic_params_default", "eic_strerror", "eic_version", "eic_graph_create", "eic_graph_info",
            "eic_graph_export", "eic_graph_memory", "eic_graph_destroy", "eic_sssp", "eic_sssp_batch",
            "eic_sssp_noalloc", "eic_batch_create", "eic_batch_run", "eic_batch_wait", "eic_batch_tune",
-           "eic_batch_info", "eic_batch_destroy")
+           "eic_batch_info", "eic_batch_destroy", "eic_server_create", "eic_server_submit", "eic_server_poll",
+           "eic_server_wait", "eic_server_result", "eic_server_release", "eic_server_stats",
+           "eic_server_reset_stats", "eic_server_destroy")
 
 
 class Params(ctypes.Structure):
@@ -56,6 +58,20 @@ class Stats(ctypes.Structure):
                 ("trace_cap", ctypes.c_uint64),
                 ("trace_len", ctypes.c_uint64), ("timeline", ctypes.POINTER(ctypes.c_uint64)),
                 ("timeline_cap", ctypes.c_uint64), ("timeline_len", ctypes.c_uint64), ("kernel_ms", ctypes.c_double)]
+
+
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("groups", ctypes.c_uint32), ("ring_entries", ctypes.c_uint32), ("output_bytes", ctypes.c_uint64),
+                ("idle_us", ctypes.c_uint32), ("reserved", ctypes.c_uint32 * 5)]
+
+
+class ServerReport(ctypes.Structure):
+    _fields_ = [(f, ctypes.c_uint64) for f in ("submitted", "admitted", "completed", "queued", "in_flight",
+                                               "max_in_flight", "kernel_launches", "output_bytes_used",
+                                               "output_bytes", "scratch_bytes")] + \
+               [("groups", ctypes.c_uint32), ("blocks_per_group", ctypes.c_uint32),
+                ("latency_p50_ms", ctypes.c_double), ("latency_p99_ms", ctypes.c_double),
+                ("latency_mean_ms", ctypes.c_double), ("latency_count", ctypes.c_uint64)]
 
 
 class EicError(RuntimeError):
@@ -114,6 +130,25 @@ def load_library(path: str | None = None):
         L.eic_batch_info.restype = c_int
         L.eic_batch_destroy.argtypes = [vp]
         L.eic_batch_destroy.restype = c_int
+        L.eic_server_create.argtypes = [ctypes.POINTER(vp), u32, ctypes.POINTER(Params), ctypes.POINTER(ServerConfig),
+                                        ctypes.POINTER(vp)]
+        L.eic_server_create.restype = c_int
+        L.eic_server_submit.argtypes = [vp, u32, u32, ctypes.POINTER(u64)]
+        L.eic_server_submit.restype = c_int
+        L.eic_server_poll.argtypes = [vp, u64, ctypes.POINTER(c_int)]
+        L.eic_server_poll.restype = c_int
+        L.eic_server_wait.argtypes = [vp, u64, u32, ctypes.POINTER(c_int)]
+        L.eic_server_wait.restype = c_int
+        L.eic_server_result.argtypes = [vp, u64, vp, ctypes.POINTER(vp), ctypes.POINTER(ctypes.c_double)]
+        L.eic_server_result.restype = c_int
+        L.eic_server_release.argtypes = [vp, u64]
+        L.eic_server_release.restype = c_int
+        L.eic_server_stats.argtypes = [vp, ctypes.POINTER(ServerReport)]
+        L.eic_server_stats.restype = c_int
+        L.eic_server_reset_stats.argtypes = [vp]
+        L.eic_server_reset_stats.restype = c_int
+        L.eic_server_destroy.argtypes = [vp]
+        L.eic_server_destroy.restype = c_int
         _lib = L
         return L
 
@@ -311,6 +346,74 @@ class Batch:
     def close(self):
         if getattr(self, "_h", None) and self._h.value and _lib is not None:
             _lib.eic_batch_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Continuous-batching request loop over resident graphs (eic_server_*)."""
+
+    def __init__(self, graphs, params: Params | None = None, groups: int = 0, ring_entries: int = 0,
+                 output_bytes: int = 0, idle_us: int = 0):
+        L = load_library()
+        self._graphs = list(graphs)  # the server reads them until it is closed
+        harr = (ctypes.c_void_p * len(self._graphs))(*[g.handle.value for g in self._graphs])
+        cfg = ServerConfig(groups=groups, ring_entries=ring_entries, output_bytes=output_bytes, idle_us=idle_us)
+        self._h = ctypes.c_void_p()
+        _check(L.eic_server_create(harr, len(self._graphs), ctypes.byref(params) if params is not None else None,
+                                   ctypes.byref(cfg), ctypes.byref(self._h)), "eic_server_create")
+
+    def submit(self, graph: int, source: int) -> int:
+        t = ctypes.c_uint64()
+        _check(load_library().eic_server_submit(self._h, graph, source, ctypes.byref(t)), "eic_server_submit")
+        return t.value
+
+    def poll(self, ticket: int):
+        """Status once done, else None."""
+        st = ctypes.c_int()
+        rc = load_library().eic_server_poll(self._h, ticket, ctypes.byref(st))
+        if rc == EBUSY:
+            return None
+        _check(rc, "eic_server_poll")
+        return st.value
+
+    def wait(self, ticket: int, timeout_ms: int = 60000) -> int:
+        st = ctypes.c_int()
+        _check(load_library().eic_server_wait(self._h, ticket, timeout_ms, ctypes.byref(st)), "eic_server_wait")
+        return st.value
+
+    def result(self, ticket: int, n: int | None = None, to_host: bool = True):
+        """(distances as a host uint32 array or None, latency in ms) of a done request."""
+        lat = ctypes.c_double()
+        if to_host:
+            if n is None:
+                raise ValueError("n is required to copy the result to the host")
+            out = np.empty(n, dtype=np.uint32)
+            _check(load_library().eic_server_result(self._h, ticket, out.ctypes.data, None, ctypes.byref(lat)),
+                   "eic_server_result")
+            return out, lat.value
+        _check(load_library().eic_server_result(self._h, ticket, None, None, ctypes.byref(lat)), "eic_server_result")
+        return None, lat.value
+
+    def release(self, ticket: int):
+        _check(load_library().eic_server_release(self._h, ticket), "eic_server_release")
+
+    def stats(self) -> dict:
+        r = ServerReport()
+        _check(load_library().eic_server_stats(self._h, ctypes.byref(r)), "eic_server_stats")
+        return {f: getattr(r, f) for f, _ in ServerReport._fields_}
+
+    def reset_stats(self):
+        _check(load_library().eic_server_reset_stats(self._h), "eic_server_reset_stats")
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value and _lib is not None:
+            _lib.eic_server_destroy(self._h)
             self._h = ctypes.c_void_p()
 
     def __del__(self):

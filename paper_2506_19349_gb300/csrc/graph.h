@@ -5,6 +5,10 @@
 
 #include "common.cuh"
 
+// Smallest accepted heavy_min: a window longer than it yields at most len / 16
+// tasks, which bounds every task list at 2m / 16 entries.
+constexpr uint32_t kHeavyMinFloor = 16;
+
 // A window of at most kTaskLen adjacency entries relaxed by one warp in a
 // round's task phase.
 struct Task {
@@ -39,12 +43,43 @@ struct Ctl {
   uint32_t tcnt[3];  // tasks of the round, by round id mod 3
   uint32_t s2_done;
   uint32_t next_q;  // batch: the query the group's first block claimed
+  unsigned long long next_ticket;  // serving: the request the group's first block claimed
   uint32_t acc_maxd;
   unsigned long long acc_deg;
   uint32_t acc_any;
   unsigned long long cnt_rounds, cnt_frontier, cnt_trav, cnt_pulls, cnt_improved, cnt_heavy, cnt_pitems;
   GridBarrier bar;
   int status;
+};
+
+// One query of a batch: graph, caller's output buffer, source, and the
+// graph-dependent layout of the statistics ring and task list.
+struct BatchQuery {
+  DevGraph G;
+  uint32_t* out;
+  uint32_t s;
+  uint32_t ring_mask, ring_shift, task_cap;
+};
+
+// Scratch of one block group, reused by every query the group runs.
+struct BatchSlot {
+  uint32_t* idist;
+  uint32_t* fbits;
+  uint32_t* cursor;
+  uint32_t* q0;
+  uint32_t* q1;
+  uint32_t* sid;
+  uint32_t* sd;
+  uint32_t* scur;
+  uint2* srow;
+  uint32_t* touched;
+  uint32_t* sbits;
+  uint32_t* hist;
+  unsigned long long* ring;
+  Task* tasks;
+  int64_t* step_ub;
+  uint32_t* step_off;
+  Ctl* ctl;
 };
 
 struct Workspace {

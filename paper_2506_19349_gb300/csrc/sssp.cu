@@ -37,6 +37,8 @@
 #include <vector>
 
 #include "graph.h"
+#include "pool.h"
+#include "serve.h"
 #include "stats.cuh"
 
 using namespace eic;
@@ -1134,36 +1136,6 @@ __global__ void k_parent(DevGraph G, const uint32_t* __restrict__ idist, uint32_
 
 // ------------------------------------------------------------- batched queries
 
-// One query of a batch: graph, caller's output buffer, source, and the
-// graph-dependent layout of the statistics ring and task list.
-struct BatchQuery {
-  DevGraph G;
-  uint32_t* out;
-  uint32_t s;
-  uint32_t ring_mask, ring_shift, task_cap;
-};
-
-// Scratch of one block group, reused by every query the group runs.
-struct BatchSlot {
-  uint32_t* idist;
-  uint32_t* fbits;
-  uint32_t* cursor;
-  uint32_t* q0;
-  uint32_t* q1;
-  uint32_t* sid;
-  uint32_t* sd;
-  uint32_t* scur;
-  uint2* srow;
-  uint32_t* touched;
-  uint32_t* sbits;
-  uint32_t* hist;
-  unsigned long long* ring;
-  Task* tasks;
-  int64_t* step_ub;
-  uint32_t* step_off;
-  Ctl* ctl;
-};
-
 struct BatchArgs {
   const BatchQuery* q;    // [nq], in the order groups claim them
   const BatchSlot* slot;  // [gridDim.x / nb]
@@ -1289,6 +1261,202 @@ __global__ void k_batch_prep(BatchArgs P, uint32_t groups) {
   if (g == 0) *P.queue = 0;
 }
 
+// ------------------------------------------------------------- serving kernel
+
+__device__ __forceinline__ unsigned long long ld_acquire_sys_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.sys.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ unsigned long long ld_relaxed_sys_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.relaxed.sys.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ uint32_t ld_relaxed_sys_u32(const uint32_t* p) {
+  uint32_t v;
+  asm volatile("ld.relaxed.sys.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void st_release_sys_u64(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.release.sys.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+constexpr unsigned long long kNoTicket = ~0ull;      // the group leaves
+constexpr unsigned long long kRetry = ~0ull - 1;      // nothing yet: the group waits again
+
+// Continuous batching: the grid is cut into groups of nb blocks; each group's
+// first thread claims the next admitted request from the ring, the group runs
+// it with its own scratch, writes the result into the request's buffer and
+// publishes the completion, then claims again. A first thread with nothing to
+// claim waits at most poll_ns at a time (its group then passes its barrier
+// and waits again, so no barrier wait comes near its bound). After idle_ns
+// without work, once no group runs a request, a group registers as idle; when
+// every group is registered they all leave together (the host relaunches the
+// kernel when work arrives). They also leave when the host sets stop. A group
+// stops at its first failing request (whose completion carries the error) and
+// counts as idle from then on.
+__global__ void __launch_bounds__(kMaxBlock, 2) k_eic_serve(ServeArgs P) {
+  __shared__ QueryShared Q;
+  __shared__ KArgs sA;
+  __shared__ unsigned long long sh_t;
+  const uint32_t grp = blockIdx.x / P.nb, qb = blockIdx.x % P.nb;
+  const BatchSlot& W = P.slot[grp];
+  Ctl* c = W.ctl;
+  unsigned long long* claim = &P.claim[0];
+  unsigned long long* finished = &P.claim[1];
+  unsigned long long* idle_groups = &P.claim[2];
+  unsigned long long* leave = &P.claim[3];
+  uint32_t gen = __ldcg(&c->bar.gen);
+  unsigned long long mine = kNoTicket;  // first thread: the request it claimed last
+  bool reported = true;                 // first thread: that request's completion is published
+  bool registered = false;              // first thread: this group counts as idle
+  for (;;) {
+    if (qb == 0 && threadIdx.x == 0) {
+      unsigned long long got = kRetry;
+      if (ld_volatile_int(&c->status) != 0) got = kNoTicket;
+      const unsigned long long t0 = globaltimer_ns();
+      while (got == kRetry) {  // bounded: poll_ns per pass
+        if (*(volatile uint32_t*)&P.ring->stop || atomicAdd(leave, 0ull) != 0) {
+          got = kNoTicket;
+          break;
+        }
+        const unsigned long long head = ld_acquire_sys_u64(&P.ring->head);
+        const unsigned long long cur = atomicAdd(claim, 0ull);
+        if (cur < head) {
+          if (atomicCAS(claim, cur, cur + 1) == cur) {
+            got = cur;
+            if (registered) {
+              atomicAdd(idle_groups, ~0ull);  // minus one
+              registered = false;
+            }
+          }
+          continue;
+        }
+        const unsigned long long waited = globaltimer_ns() - t0;
+        if (!registered && waited > P.idle_ns && atomicAdd(finished, 0ull) == cur) {
+          atomicAdd(idle_groups, 1ull);
+          registered = true;
+        }
+        if (registered && atomicAdd(idle_groups, 0ull) >= P.groups) {
+          atomicExch(leave, 1ull);
+          got = kNoTicket;
+          break;
+        }
+        if (waited > P.poll_ns) break;  // kRetry
+        __nanosleep(256);
+      }
+      c->next_ticket = got;
+      if (got != kNoTicket && got != kRetry) {
+        mine = got;
+        reported = false;
+      }
+    }
+    if (!grid_barrier(&c->bar, &gen, P.nb, P.max_spin, &c->status)) break;
+    if (threadIdx.x == 0) sh_t = __ldcg(&c->next_ticket);
+    __syncthreads();
+    const unsigned long long t = sh_t;
+    if (t == kNoTicket) break;
+    if (t == kRetry) continue;
+    const uint32_t e = (uint32_t)(t & (P.cap - 1));
+    if (threadIdx.x == 0) {  // the entry was published before head (host release, leader acquire)
+      const ServeRequest* rq = &P.req[e];
+      const uint32_t gi = ld_relaxed_sys_u32(&rq->graph);
+      const uint32_t src = ld_relaxed_sys_u32(&rq->source);
+      uint32_t* out = (uint32_t*)ld_relaxed_sys_u64((const unsigned long long*)&rq->out);
+      const BatchQuery& bq = P.graphs[gi < P.num_graphs ? gi : 0];  // the host admits valid ids only
+      sA.G = bq.G;
+      sA.dist = W.idist;
+      sA.out = out;
+      sA.fbits = W.fbits;
+      sA.fwords = bq.G.ni / 32 + 2;
+      sA.cursor = W.cursor;
+      sA.q0 = W.q0;
+      sA.q1 = W.q1;
+      sA.sid = W.sid;
+      sA.sd = W.sd;
+      sA.scur = W.scur;
+      sA.srow = W.srow;
+      sA.touched = W.touched;
+      sA.sbits = W.sbits;
+      sA.hist = W.hist;
+      sA.ring = W.ring;
+      sA.tasks = W.tasks;
+      sA.step_ub = W.step_ub;
+      sA.step_off = W.step_off;
+      sA.trace = nullptr;
+      sA.ctl = c;
+      sA.status_out = nullptr;
+      sA.s = src;
+      sA.alpha = P.alpha;
+      sA.beta = P.beta;
+      sA.st_num = P.st_num;
+      sA.gap_shift = P.gap_shift;
+      sA.heavy_min = P.heavy_min;
+      sA.max_spin = P.max_spin;
+      sA.flags = P.flags;
+      sA.ring_mask = bq.ring_mask;
+      sA.ring_shift = bq.ring_shift;
+      sA.task_cap = bq.task_cap;
+      sA.step_cap = P.step_cap;
+      sA.trace_cap = 0;
+      sA.timeline = nullptr;
+      sA.timeline_cap = 0;
+      sA.nb = P.nb;
+    }
+    __syncthreads();
+    if (!query_setup(sA, gen)) break;
+    run_query(sA, Q, gen);
+    __syncthreads();
+    if (ld_volatile_int(&c->status) != 0) break;
+    query_output(sA);
+    // every block's part of the result is written before the group reports
+    if (!grid_barrier(&c->bar, &gen, P.nb, P.max_spin, &c->status)) break;
+    if (qb == 0 && threadIdx.x == 0) {
+      __threadfence_system();
+      P.done[e].status = EIC_OK;
+      st_release_sys_u64(&P.done[e].ticket_plus1, t + 1);
+      atomicAdd(finished, 1ull);
+      reported = true;
+    }
+  }
+  if (qb == 0 && threadIdx.x == 0) {
+    if (!reported) {  // a request the group claimed and stopped in reports the group's error
+      const unsigned long long t = mine;
+      const uint32_t e = (uint32_t)(t & (P.cap - 1));
+      const int st = ld_volatile_int(&c->status);
+      __threadfence_system();
+      P.done[e].status = st != 0 ? st : EIC_ETIMEOUT;
+      st_release_sys_u64(&P.done[e].ticket_plus1, t + 1);
+      atomicAdd(finished, 1ull);
+    }
+    // a group that stopped early counts as idle, so the others can leave
+    if (!registered && atomicAdd(leave, 0ull) == 0) atomicAdd(idle_groups, 1ull);
+  }
+}
+
+// Starting state of every group's barrier and status, and of the idle vote.
+__global__ void k_serve_prep(const BatchSlot* slot, uint32_t groups, unsigned long long* claim) {
+  const uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g < groups) {
+    slot[g].ctl->bar.count = 0;
+    slot[g].ctl->status = 0;
+  }
+  if (g == 0) {
+    claim[2] = 0;
+    claim[3] = 0;
+  }
+}
+
 }  // namespace
 
 // ------------------------------------------------------------------ host
@@ -1298,7 +1466,6 @@ namespace {
 constexpr uint32_t kStepCap = 1u << 20;     // steps per query
 constexpr uint32_t kTraceCap = 1u << 16;    // trace rows kept on the device
 constexpr uint32_t kTimelineCap = 1u << 16; // diagnostic timeline events
-constexpr uint32_t kHeavyMinFloor = 16;     // smallest accepted heavy_min (bounds the task list)
 constexpr uint32_t kHeavyMinCeil = 4096;
 constexpr uint32_t kDefaultHeavyMin = 32;
 constexpr int kDefaultBlock = 512;
@@ -1592,129 +1759,6 @@ int eic_sssp(const eic_graph* gc, uint32_t source, uint32_t* dist, uint32_t* par
 // ------------------------------------------------------------ batch host side
 
 namespace {
-
-constexpr uint32_t kBatchStepCap = 1u << 17;  // steps per query of a batch
-constexpr double kBatchMemFrac = 0.8;         // share of free device memory the scratch may take
-
-// Capacities one block group's scratch must cover.
-struct SlotCaps {
-  uint64_t ni = 0, two_m = 0;
-  uint32_t D = 0, ring_bits = 0;
-  bool covers(const SlotCaps& o) const {
-    return ni >= o.ni && two_m >= o.two_m && D >= o.D && ring_bits >= o.ring_bits;
-  }
-};
-
-// Byte offsets of one group's arrays inside its slot (256-byte aligned).
-struct SlotLayout {
-  uint64_t idist, fbits, cursor, q0, q1, sid, sd, scur, srow, touched, sbits, hist, ring, tasks, step_ub, step_off,
-      ctl, bytes;
-};
-
-SlotLayout slot_layout(const SlotCaps& c) {
-  SlotLayout L;
-  uint64_t o = 0;
-  auto take = [&o](uint64_t bytes) {
-    const uint64_t at = o;
-    o += (bytes + 255) & ~255ull;
-    return at;
-  };
-  const uint64_t n = c.ni, words = n / 32 + 2;
-  L.idist = take(n * 4);
-  L.fbits = take(2 * words * 4);
-  L.cursor = take(n * 4);
-  L.q0 = take(n * 4);
-  L.q1 = take(n * 4);
-  L.sid = take((n + 2) * 4);
-  L.sd = take((n + 2) * 4);
-  L.scur = take((n + 2) * 4);
-  L.srow = take((n + 2) * 8);
-  L.touched = take((n + 1) * 4);
-  L.sbits = take(words * 4);
-  L.hist = take(((uint64_t)c.D + 1) * 4);
-  L.ring = take((1ull << c.ring_bits) * 8);
-  L.tasks = take((c.two_m / kHeavyMinFloor + 2) * sizeof(Task));
-  L.step_ub = take(((uint64_t)kBatchStepCap + 2) * 8);
-  L.step_off = take(((uint64_t)kBatchStepCap + 2) * 4);
-  L.ctl = take(sizeof(Ctl));
-  L.bytes = o;
-  return L;
-}
-
-// Scratch of `count` block groups in one device allocation.
-struct SlotPool {
-  unsigned char* base = nullptr;
-  BatchSlot* d_slots = nullptr;
-  SlotCaps caps;
-  uint32_t count = 0;
-  uint64_t slot_bytes = 0;
-
-  void release() {
-    cudaFree(base);
-    cudaFree(d_slots);
-    base = nullptr;
-    d_slots = nullptr;
-    caps = SlotCaps();
-    count = 0;
-    slot_bytes = 0;
-  }
-
-  int ensure(const SlotCaps& need, uint32_t groups) {
-    if (base && count >= groups && caps.covers(need)) return EIC_OK;
-    release();
-    const SlotLayout L = slot_layout(need);
-    if (cudaMalloc((void**)&base, L.bytes * groups) != cudaSuccess ||
-        cudaMalloc((void**)&d_slots, sizeof(BatchSlot) * groups) != cudaSuccess) {
-      (void)cudaGetLastError();
-      release();
-      return EIC_ENOMEM;
-    }
-    std::vector<BatchSlot> h(groups);
-    for (uint32_t g = 0; g < groups; ++g) {
-      unsigned char* b = base + (uint64_t)g * L.bytes;
-      BatchSlot& s = h[g];
-      s.idist = (uint32_t*)(b + L.idist);
-      s.fbits = (uint32_t*)(b + L.fbits);
-      s.cursor = (uint32_t*)(b + L.cursor);
-      s.q0 = (uint32_t*)(b + L.q0);
-      s.q1 = (uint32_t*)(b + L.q1);
-      s.sid = (uint32_t*)(b + L.sid);
-      s.sd = (uint32_t*)(b + L.sd);
-      s.scur = (uint32_t*)(b + L.scur);
-      s.srow = (uint2*)(b + L.srow);
-      s.touched = (uint32_t*)(b + L.touched);
-      s.sbits = (uint32_t*)(b + L.sbits);
-      s.hist = (uint32_t*)(b + L.hist);
-      s.ring = (unsigned long long*)(b + L.ring);
-      s.tasks = (Task*)(b + L.tasks);
-      s.step_ub = (int64_t*)(b + L.step_ub);
-      s.step_off = (uint32_t*)(b + L.step_off);
-      s.ctl = (Ctl*)(b + L.ctl);
-      if (cudaMemset(s.ctl, 0, sizeof(Ctl)) != cudaSuccess) {
-        (void)cudaGetLastError();
-        release();
-        return EIC_ECUDA;
-      }
-    }
-    if (cudaMemcpy(d_slots, h.data(), sizeof(BatchSlot) * groups, cudaMemcpyHostToDevice) != cudaSuccess) {
-      (void)cudaGetLastError();
-      release();
-      return EIC_ECUDA;
-    }
-    caps = need;
-    count = groups;
-    slot_bytes = L.bytes;
-    return EIC_OK;
-  }
-};
-
-uint32_t ring_layout(uint32_t maxw, uint32_t* shift) {
-  const uint32_t m = maxw ? maxw : 1;
-  uint32_t bits = 0;
-  while (bits < 32 && (1ull << bits) <= m) ++bits;  // 2^bits > maxW
-  *shift = bits > 20 ? bits - 20 : 0;
-  return bits < 20 ? bits : 20;
-}
 
 int batch_grid(int block, uint32_t* grid) {
   int dev = 0, sms = 0, per_sm = 0, coop = 0;
@@ -2284,4 +2328,28 @@ extern "C" int eic_sssp_noalloc(const eic_graph* gc, uint32_t source, uint32_t* 
   EIC_CUDA_TRY(cudaMemcpyAsync(&status, &ctl->status, sizeof(int), cudaMemcpyDeviceToHost, st));
   EIC_CUDA_TRY(cudaStreamSynchronize(st));
   return status;
+}
+
+// ------------------------------------------------------------ serving launch
+
+int eic_serve_grid(int block, uint32_t* grid) {
+  int dev = 0, sms = 0, per_sm = 0, coop = 0;
+  EIC_CUDA_TRY(cudaGetDevice(&dev));
+  EIC_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  EIC_CUDA_TRY(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
+  if (!coop) return EIC_ECUDA;
+  EIC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_eic_serve, block, 0));
+  if (per_sm < 1) return EIC_ECUDA;
+  *grid = (uint32_t)(sms * per_sm);
+  return EIC_OK;
+}
+
+int eic_serve_launch(const ServeArgs& args, uint32_t groups, uint32_t block, cudaStream_t stream) {
+  k_serve_prep<<<(groups + 255) / 256, 256, 0, stream>>>(args.slot, groups, args.claim);
+  EIC_CUDA_TRY(cudaGetLastError());
+  ServeArgs a = args;
+  void* kargs[] = {&a};
+  EIC_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)k_eic_serve, dim3(groups * args.nb), dim3(block), kargs, 0,
+                                           stream));
+  return EIC_OK;
 }

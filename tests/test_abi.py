@@ -62,6 +62,17 @@ def test_host_only_calls(lib):
     assert lib.eic_batch_tune(None, None, None) == binding.EINVAL
     assert lib.eic_batch_info(None, None) == binding.EINVAL
     assert lib.eic_batch_destroy(None) == binding.OK
+    t = ctypes.c_uint64()
+    assert lib.eic_server_create(None, 0, None, None, ctypes.byref(out)) == binding.EINVAL
+    assert lib.eic_server_create(None, 1, None, None, None) == binding.EINVAL
+    assert lib.eic_server_submit(None, 0, 0, ctypes.byref(t)) == binding.EINVAL
+    assert lib.eic_server_poll(None, 0, None) == binding.EINVAL
+    assert lib.eic_server_wait(None, 0, 1, None) == binding.EINVAL
+    assert lib.eic_server_result(None, 0, None, None, None) == binding.EINVAL
+    assert lib.eic_server_release(None, 0) == binding.EINVAL
+    assert lib.eic_server_stats(None, None) == binding.EINVAL
+    assert lib.eic_server_reset_stats(None) == binding.EINVAL
+    assert lib.eic_server_destroy(None) == binding.OK
 
 
 def test_struct_layouts_match_the_header():
@@ -89,7 +100,11 @@ def test_ctypes_mirrors_match_the_c_layout(tmp_path):
               "eic_step": (binding.Step, ["lb", "ub", "st", "gap_lb", "sumd_lb", "highd_lb", "rounds", "settled"]),
               "eic_stats": (binding.Stats, ["steps", "pull_items", "trace", "trace_cap", "trace_len", "timeline",
                                             "timeline_cap", "timeline_len", "kernel_ms"]),
-              "eic_batch_config": (binding.BatchConfig, ["groups", "queries", "scratch_bytes", "tuned_ms"])}
+              "eic_batch_config": (binding.BatchConfig, ["groups", "queries", "scratch_bytes", "tuned_ms"]),
+              "eic_server_config": (binding.ServerConfig, ["groups", "ring_entries", "output_bytes", "idle_us",
+                                                            "reserved"]),
+              "eic_server_report": (binding.ServerReport, ["submitted", "kernel_launches", "scratch_bytes", "groups",
+                                                            "blocks_per_group", "latency_p50_ms", "latency_count"])}
     lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "eic.h"', "int main(void) {"]
     for st, (_, fields) in checks.items():
         lines.append(f'  printf("{st} %zu\\n", sizeof({st}));')
