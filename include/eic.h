@@ -106,7 +106,8 @@ typedef struct {
    * uint64, it receives (device globaltimer ns, tag) pairs: one per grid
    * barrier and around each step-boundary evaluation. tag = kind << 32 |
    * round id, kind 0 kernel start, 1 round, 2 heavy phase, 3 step, 4/5
-   * step-boundary begin/end. */
+   * step-boundary begin/end; kind 8 and 9 carry the round's item and task
+   * counts in place of the round id. */
   uint64_t* timeline;
   uint64_t timeline_cap;
   uint64_t timeline_len;

@@ -96,6 +96,7 @@ constexpr uint32_t kMaxBlock = 512;
 constexpr uint32_t kMaxWarps = kMaxBlock / 32;
 constexpr uint32_t kTaskLen = 64;     // adjacency entries per grid task
 constexpr uint32_t kCursorMin = 16;   // rows longer than this keep a window cursor
+constexpr uint32_t kPullFast = 4;     // pull prefixes shorter than this are answered by their lane
 constexpr uint32_t kStageT = 1024;    // tasks staged per block
 constexpr uint32_t kStageQ = 4096;    // next-frontier appends staged per block
 constexpr uint32_t kStageF = 4096;    // settled-list appends staged per block
@@ -183,12 +184,41 @@ __device__ __forceinline__ void tl_block(const KArgs& A, uint32_t kind, uint32_t
 
 __device__ __forceinline__ int64_t d64(uint32_t d) { return d == EIC_INF ? EIC_INF_T : (int64_t)d; }
 
+// Streaming reads (adjacency entries, the pull list) carry an L2 evict-first
+// policy, so that the per-vertex arrays (dist, row offsets, bitmaps, cursors)
+// stay in L2 while the adjacency streams past.
+__device__ __forceinline__ uint64_t stream_policy() {
+  uint64_t pol;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
+
+__device__ __forceinline__ uint2 ld_stream(const uint2* p) {
+  uint2 v;
+  asm("ld.global.nc.L2::cache_hint.v2.u32 {%0, %1}, [%2], %3;" : "=r"(v.x), "=r"(v.y) : "l"(p), "l"(stream_policy()));
+  return v;
+}
+
+__device__ __forceinline__ uint32_t ld_stream_w(const uint2* p) {
+  uint32_t v;
+  asm("ld.global.nc.L2::cache_hint.u32 %0, [%1], %2;" : "=r"(v) : "l"(&p->y), "l"(stream_policy()));
+  return v;
+}
+
+__device__ __forceinline__ uint4 ld_stream4(const uint4* p) {
+  uint4 v;
+  asm("ld.global.nc.L2::cache_hint.v4.u32 {%0, %1, %2, %3}, [%4], %5;"
+      : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+      : "l"(p), "l"(stream_policy()));
+  return v;
+}
+
 // first index in [b, e) of the weight-sorted row with weight >= t
 __device__ __forceinline__ uint32_t lower_bound_w(const uint2* __restrict__ adj, uint32_t b, uint32_t e, int64_t t) {
   if (t <= 1) return b;  // weights are >= 1
   while (b < e) {
     uint32_t mid = b + ((e - b) >> 1);
-    if ((int64_t)__ldg(&adj[mid].y) < t)
+    if ((int64_t)ld_stream_w(&adj[mid]) < t)
       b = mid + 1;
     else
       e = mid;
@@ -201,7 +231,7 @@ __device__ __forceinline__ uint32_t lower_bound_w(const uint2* __restrict__ adj,
 // O(log distance), and a short window costs one or two probes of one sector.
 __device__ __forceinline__ uint32_t gallop_w(const uint2* __restrict__ adj, uint32_t p, uint32_t e, int64_t t) {
   if (t <= 1 || p >= e) return p;
-  if ((int64_t)__ldg(&adj[p].y) >= t) return p;
+  if ((int64_t)ld_stream_w(&adj[p]) >= t) return p;
   uint32_t lo = p;  // weight at lo < t
   uint32_t hi;
   uint64_t step = 1;
@@ -211,7 +241,7 @@ __device__ __forceinline__ uint32_t gallop_w(const uint2* __restrict__ adj, uint
       hi = e;
       break;
     }
-    if ((int64_t)__ldg(&adj[h].y) >= t) {
+    if ((int64_t)ld_stream_w(&adj[h]) >= t) {
       hi = (uint32_t)h;
       break;
     }
@@ -342,6 +372,9 @@ __device__ void round_phase(const KArgs& A, const RoundCtx& R, const Local& L, R
   for (uint32_t base = gwarp * 32; base < nitems; base += nwarps * 32) {
     const uint32_t i = base + lane;
     uint32_t u = 0, val = EIC_INF, b = 0, len = 0, mode = kModePush;
+    uint32_t pfast = EIC_INF;       // best pull candidate of the lane's vertex
+    bool plong = false;             // its prefix is longer than kPullFast entries
+    uint32_t pbeg = 0, pend = 0;    // the rest of its row, scanned by the warp
     if (i < nitems) {
       if (!round1 || i >= npp) {  // frontier vertex (or the source, once)
         u = round1 ? L.s_int : __ldcg(&qin[i]);
@@ -377,17 +410,68 @@ __device__ void round_phase(const KArgs& A, const RoundCtx& R, const Local& L, R
           }
         }
       } else {  // pull set: unsettled, smallest weight < ub - st (Function 1)
-        const uint4 z = __ldg(&A.G.nz[i - np]);
+        const uint4 z = ld_stream4(&A.G.nz[i - np]);
         u = z.x;
         mode = kModePull;
+        // the settled bit and the row's first kPullFast entries, loaded together
+        const uint32_t rl = z.w - z.z;
         const uint32_t bits = __ldcg(&A.sbits[u >> 5]);
-        if (!((bits >> (u & 31)) & 1u)) {
+        if (!((bits >> (u & 31)) & 1u)) {  // unsettled: its row's first kPullFast entries, together
+          uint2 ent[kPullFast];
+#pragma unroll
+          for (uint32_t k = 0; k < kPullFast; ++k)
+            ent[k] = k < rl ? ld_stream(&A.G.adj[z.z + k]) : make_uint2(0u, EIC_INF);
           C.pitems += 1;
-          // the row's first weight is below the bound (nz order): gallop from the second
-          b = z.z;
-          len = gallop_w(A.G.adj, b + 1, z.w, pull_bound) - b;
+          uint32_t c = 0;  // the prefix with w < ub - st (rows are weight-sorted; the first entry is in it)
+#pragma unroll
+          for (uint32_t k = 0; k < kPullFast; ++k) c += (k < rl && (int64_t)ent[k].y < pull_bound) ? 1u : 0u;
+          plong = c == kPullFast && rl > kPullFast;  // the prefix goes on: the warp scans the rest
+          {  // the loaded part of the prefix, answered in the lane
+            uint32_t dv[kPullFast];
+#pragma unroll
+            for (uint32_t k = 0; k < kPullFast; ++k) dv[k] = k < c ? __ldcg(&A.dist[ent[k].x]) : EIC_INF;
+#pragma unroll
+            for (uint32_t k = 0; k < kPullFast; ++k) {
+              if (k >= c) continue;
+              C.trav += 1;
+              C.pulls += 1;
+              const int64_t dvv = dv[k];
+              if (dv[k] != EIC_INF && dvv >= R.st && dvv < R.lb && dvv + ent[k].y < R.ub)
+                pfast = min(pfast, (uint32_t)(dvv + ent[k].y));
+            }
+          }
+          if (plong) {
+            pbeg = z.z + kPullFast;
+            pend = z.w;
+          }
         }
       }
+    }
+    // long pull prefixes, one lane's row at a time: coalesced 32-entry chunks
+    // while the whole chunk is below the bound (no search for the prefix end)
+    for (uint32_t lm = __ballot_sync(EIC_FULL_MASK, plong); lm; lm &= lm - 1) {
+      const uint32_t sl = __ffs(lm) - 1;
+      const uint32_t cb = __shfl_sync(EIC_FULL_MASK, pbeg, sl), ce = __shfl_sync(EIC_FULL_MASK, pend, sl);
+      uint32_t best = EIC_INF;
+      for (uint32_t base = cb; base < ce; base += 32) {
+        const uint32_t j = base + lane;
+        bool in = false;
+        if (j < ce) {
+          const uint2 e2 = ld_stream(&A.G.adj[j]);
+          in = (int64_t)e2.y < pull_bound;
+          if (in) {
+            C.trav += 1;
+            C.pulls += 1;
+            const uint32_t dv = __ldcg(&A.dist[e2.x]);
+            const int64_t dvv = dv;
+            if (dv != EIC_INF && dvv >= R.st && dvv < R.lb && dvv + e2.y < R.ub)
+              best = min(best, (uint32_t)(dvv + e2.y));
+          }
+        }
+        if (!__all_sync(EIC_FULL_MASK, in || j >= ce)) break;  // the prefix ended in this chunk
+      }
+      for (int o = 16; o > 0; o >>= 1) best = min(best, __shfl_xor_sync(EIC_FULL_MASK, best, o));
+      if (lane == sl) pfast = min(pfast, best);
     }
     if (len > A.heavy_min) {
       emit_tasks(A, R, T, b, len, u, mode == kModePull ? kNone : val);
@@ -398,7 +482,7 @@ __device__ void round_phase(const KArgs& A, const RoundCtx& R, const Local& L, R
     const uint32_t total = __shfl_sync(EIC_FULL_MASK, incl, 31);
     W.beg[lane] = b;
     W.excl[lane] = incl - len;
-    W.val[lane] = mode == kModePull ? EIC_INF : val;
+    W.val[lane] = mode == kModePull ? pfast : val;
     W.u[lane] = u;
     W.mode[lane] = mode;
     __syncwarp();
@@ -415,7 +499,7 @@ __device__ void round_phase(const KArgs& A, const RoundCtx& R, const Local& L, R
           else
             hi = mid - 1;
         }
-        const uint2 ent = __ldg(&A.G.adj[W.beg[lo] + (g - W.excl[lo])]);
+        const uint2 ent = ld_stream(&A.G.adj[W.beg[lo] + (g - W.excl[lo])]);
         v = ent.x;
         if (W.mode[lo] != kModePull) {
           C.trav += 1;
@@ -466,7 +550,7 @@ __device__ void task_phase(const KArgs& A, const RoundCtx& R, uint32_t ntasks, S
         bool ok = false;
         uint32_t v = 0, nd = 0, old = 0;
         if (j < tk.len) {
-          const uint2 ent = __ldg(&A.G.adj[tk.beg + j]);
+          const uint2 ent = ld_stream(&A.G.adj[tk.beg + j]);
           v = ent.x;
           nd = tk.d + ent.y;
           C.trav += 1;
@@ -484,7 +568,7 @@ __device__ void task_phase(const KArgs& A, const RoundCtx& R, uint32_t ntasks, S
       for (uint32_t h = 0; h < 2; ++h) {
         const uint32_t j = lane + 32 * h;
         if (j < tk.len) {
-          const uint2 ent = __ldg(&A.G.adj[tk.beg + j]);
+          const uint2 ent = ld_stream(&A.G.adj[tk.beg + j]);
           if ((int64_t)ent.y < pull_bound) {
             C.trav += 1;
             C.pulls += 1;
@@ -873,6 +957,7 @@ __device__ void run_query(const KArgs& A, QueryShared& Q, uint32_t& gen) {
       Local LL = L;
       if (!L.pull_on) LL.pull_cnt = 0;
       const uint32_t nitems = round1 ? (LL.push_end - LL.push_beg) + LL.pull_cnt + LL.extra_s : L.cur_cnt;
+      if (qb == 0 && threadIdx.x == 0) tl_mark(A, 8, nitems);  // diagnostic: the round's items
       round_phase(A, R, LL, P.r, T, nitems, round1, qin, C);
       if (!grid_barrier(&c->bar, &gen, A.nb, A.max_spin, &c->status)) {
         alive = false;
@@ -890,6 +975,7 @@ __device__ void run_query(const KArgs& A, QueryShared& Q, uint32_t& gen) {
       uint32_t uc = (uint32_t)sh_snap[2];
       __syncthreads();
       if (hp != 0) {
+        if (qb == 0 && threadIdx.x == 0) tl_mark(A, 9, (uint32_t)hp);  // diagnostic: the round's tasks
         task_phase(A, R, (uint32_t)hp, T, C);
         if (!grid_barrier(&c->bar, &gen, A.nb, A.max_spin, &c->status)) {
           alive = false;
