@@ -205,6 +205,31 @@ __device__ __forceinline__ uint32_t ld_stream_w(const uint2* p) {
   return v;
 }
 
+// The same for lists written earlier in the kernel (frontier queue, settled
+// list, tasks): L2 only (no L1 copy that another block's write could leave
+// stale), evict-first.
+__device__ __forceinline__ uint32_t ld_list(const uint32_t* p) {
+  uint32_t v;
+  asm volatile("ld.global.cg.L2::cache_hint.u32 %0, [%1], %2;" : "=r"(v) : "l"(p), "l"(stream_policy()));
+  return v;
+}
+
+__device__ __forceinline__ uint2 ld_list2(const uint2* p) {
+  uint2 v;
+  asm volatile("ld.global.cg.L2::cache_hint.v2.u32 {%0, %1}, [%2], %3;"
+               : "=r"(v.x), "=r"(v.y)
+               : "l"(p), "l"(stream_policy()));
+  return v;
+}
+
+__device__ __forceinline__ uint4 ld_list4(const void* p) {
+  uint4 v;
+  asm volatile("ld.global.cg.L2::cache_hint.v4.u32 {%0, %1, %2, %3}, [%4], %5;"
+               : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+               : "l"(p), "l"(stream_policy()));
+  return v;
+}
+
 __device__ __forceinline__ uint4 ld_stream4(const uint4* p) {
   uint4 v;
   asm("ld.global.nc.L2::cache_hint.v4.u32 {%0, %1, %2, %3}, [%4], %5;"
@@ -369,15 +394,32 @@ __device__ void round_phase(const KArgs& A, const RoundCtx& R, const Local& L, R
   const uint32_t gwarp = qblock(A) * (nt >> 5) + warp, nwarps = A.nb * (nt >> 5);
   const int64_t pull_bound = R.ub - R.st;
   WarpScr& W = S.w[warp];
+  // an item's record: the vertex (frontier, source), {dist, row begin, row
+  // end} (push set, from the settled list) or the pull-list entry. The next
+  // iteration's record is loaded while this iteration runs.
+  auto fetch = [&](uint32_t ii) -> uint4 {
+    if (ii >= nitems) return make_uint4(0u, 0u, 0u, 0u);
+    if (!round1) return make_uint4(ld_list(&qin[ii]), 0u, 0u, 0u);
+    if (ii >= npp) return make_uint4(L.s_int, 0u, 0u, 0u);
+    if (ii < np) {
+      const uint32_t idx = L.push_beg + ii;
+      const uint2 rr = ld_list2(&A.srow[idx]);
+      return make_uint4(ld_list(&A.sd[idx]), rr.x, rr.y, 0u);
+    }
+    return ld_stream4(&A.G.nz[ii - np]);
+  };
+  uint4 pre = fetch(gwarp * 32 + lane);
   for (uint32_t base = gwarp * 32; base < nitems; base += nwarps * 32) {
     const uint32_t i = base + lane;
+    const uint4 rec = pre;
+    pre = fetch(base + nwarps * 32 + lane);
     uint32_t u = 0, val = EIC_INF, b = 0, len = 0, mode = kModePush;
     uint32_t pfast = EIC_INF;       // best pull candidate of the lane's vertex
     bool plong = false;             // its prefix is longer than kPullFast entries
     uint32_t pbeg = 0, pend = 0;    // the rest of its row, scanned by the warp
     if (i < nitems) {
       if (!round1 || i >= npp) {  // frontier vertex (or the source, once)
-        u = round1 ? L.s_int : __ldcg(&qin[i]);
+        u = rec.x;
         const uint32_t d = __ldcg(&A.dist[u]);
         const uint32_t rb = __ldg(&A.G.row[u]), re = __ldg(&A.G.row[u + 1]);
         val = d;
@@ -393,14 +435,13 @@ __device__ void round_phase(const KArgs& A, const RoundCtx& R, const Local& L, R
         }
       } else if (i < np) {  // push set: settled, lb0 <= dist <= st (all from the settled list)
         const uint32_t idx = L.push_beg + i;
-        const uint32_t d = __ldcg(&A.sd[idx]);
+        const uint32_t d = rec.x;
         val = d;
         if ((int64_t)d >= R.lb0 && (int64_t)d <= R.st) {
-          const uint2 rr = __ldcg(&A.srow[idx]);
-          const uint32_t rb = rr.x, re = rr.y;
+          const uint32_t rb = rec.y, re = rec.z;
           if (!(d > 0 && re - rb == 1)) {
             C.frontier += 1;
-            const uint32_t cur = __ldcg(&A.scur[idx]);
+            const uint32_t cur = ld_list(&A.scur[idx]);
             // windows of consecutive steps are contiguous: resume at the cursor
             b = cur == kNone ? lower_bound_w(A.G.adj, rb, re, R.lb - (int64_t)d)
                              : gallop_w(A.G.adj, rb + cur, re, R.lb - (int64_t)d);
@@ -410,7 +451,7 @@ __device__ void round_phase(const KArgs& A, const RoundCtx& R, const Local& L, R
           }
         }
       } else {  // pull set: unsettled, smallest weight < ub - st (Function 1)
-        const uint4 z = ld_stream4(&A.G.nz[i - np]);
+        const uint4 z = rec;
         u = z.x;
         mode = kModePull;
         // the settled bit and the row's first kPullFast entries, loaded together
@@ -542,7 +583,8 @@ __device__ void task_phase(const KArgs& A, const RoundCtx& R, uint32_t ntasks, S
   const uint32_t nwarps = A.nb * wpb;
   const int64_t pull_bound = R.ub - R.st;
   for (uint32_t t = qblock(A) * wpb + (threadIdx.x >> 5); t < ntasks; t += nwarps) {
-    const Task tk = A.tasks[t];
+    const uint4 tv = ld_list4(&A.tasks[t]);
+    const Task tk = {tv.x, tv.y, tv.z, tv.w};
     if (tk.d != kNone) {  // push
 #pragma unroll
       for (uint32_t h = 0; h < 2; ++h) {
@@ -1020,7 +1062,7 @@ __device__ void run_query(const KArgs& A, QueryShared& Q, uint32_t& gen) {
         bool take = false;
         uint32_t x = 0, d = 0, xrb = 0, xre = 0;
         if (idx < lend) {
-          x = __ldcg(&list[idx]);
+          x = ld_list(&list[idx]);
           d = __ldcg(&A.dist[x]);
           xrb = __ldg(&A.G.row[x]);
           xre = __ldg(&A.G.row[x + 1]);
