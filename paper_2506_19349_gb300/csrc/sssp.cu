@@ -98,8 +98,7 @@ constexpr uint32_t kTaskLen = 64;     // adjacency entries per grid task
 constexpr uint32_t kCursorMin = 16;   // rows longer than this keep a window cursor
 constexpr uint32_t kPullFast = 4;     // pull prefixes shorter than this are answered by their lane
 constexpr uint32_t kStageT = 1024;    // tasks staged per block
-constexpr uint32_t kStageQ = 4096;    // next-frontier appends staged per block
-constexpr uint32_t kStageF = 4096;    // settled-list appends staged per block
+constexpr uint32_t kWarpStage = 256;  // next-frontier / settled-list appends staged per warp
 
 struct WarpScr {  // one warp's small windows
   uint32_t beg[32];
@@ -113,14 +112,46 @@ struct RoundScr {
   WarpScr w[kMaxWarps];
 };
 
-// Appends of a block gathered in shared memory and written with one global
-// atomic per list and round; what does not fit goes out warp by warp.
+// Appends gathered in shared memory. Next-frontier and settled-list entries
+// are staged per warp and written by the warp with one global atomic per
+// kWarpStage entries (no block synchronisation); tasks are staged per block
+// and written at the end of a phase.
 struct Stage {
-  uint32_t qn, fn, tn, qbase, fbase, tbase;
-  uint32_t qbuf[kStageQ];
-  uint32_t fbuf[kStageF];
+  uint32_t tn, tbase;
   Task tbuf[kStageT];
+  uint32_t wq[kMaxWarps][kWarpStage];
+  uint32_t wf[kMaxWarps][kWarpStage];
 };
+
+// One warp's append stage for one list. n is warp-uniform.
+struct WarpList {
+  uint32_t* buf;    // shared memory, kWarpStage entries
+  uint32_t n;       // entries held
+  uint32_t* gcnt;   // the list's global count
+  uint32_t* glist;  // the list
+};
+
+__device__ __forceinline__ void warp_flush(WarpList& W) {
+  if (W.n == 0) return;
+  uint32_t base = 0;
+  if (lane_id() == 0) base = atomicAdd(W.gcnt, W.n);
+  base = __shfl_sync(EIC_FULL_MASK, base, 0);
+  __syncwarp();
+  for (uint32_t k = lane_id(); k < W.n; k += 32) __stcg(&W.glist[base + k], W.buf[k]);
+  __syncwarp();
+  W.n = 0;
+}
+
+// Warp-collective append of v for the lanes with want.
+__device__ __forceinline__ void warp_push(WarpList& W, bool want, uint32_t v) {
+  const uint32_t mask = __ballot_sync(EIC_FULL_MASK, want);
+  if (mask == 0) return;
+  const uint32_t cnt = __popc(mask);
+  if (W.n + cnt > kWarpStage) warp_flush(W);
+  if (want) W.buf[W.n + __popc(mask & ((1u << lane_id()) - 1u))] = v;
+  __syncwarp();
+  W.n += cnt;
+}
 
 struct S2Scr {
   uint32_t hist[kShRanks];
@@ -289,42 +320,18 @@ struct RoundCtx {
   uint32_t* work;
 };
 
-// Warp-collective append of v for the lanes with want: into the block's
-// shared stage while it has room, else straight to the global list.
-template <typename T>
-__device__ __forceinline__ void staged_append(bool want, T v, uint32_t* sn, T* sbuf, uint32_t cap, uint32_t* gcnt,
-                                              T* glist) {
-  const uint32_t mask = __ballot_sync(EIC_FULL_MASK, want);
-  if (mask == 0) return;
-  const uint32_t lane = lane_id(), leader = __ffs(mask) - 1;
-  uint32_t base = 0;
-  if (lane == leader) base = atomicAdd(sn, (uint32_t)__popc(mask));
-  base = __shfl_sync(EIC_FULL_MASK, base, leader);
-  const uint32_t pos = base + __popc(mask & ((1u << lane) - 1u));
-  const bool spill = want && pos >= cap;
-  if (want && !spill) sbuf[pos] = v;
-  const uint32_t slot = warp_append(spill, gcnt);
-  if (spill) __stcg(&glist[slot], v);
-}
-
-// Flush the block's stages to the global lists (block-uniform call).
+// Flush the block's task stage to the global list (block-uniform call).
 __device__ __forceinline__ void stage_flush(Stage& T, const RoundCtx& R, Task* tasks) {
   __syncthreads();
   if (threadIdx.x == 0) {
-    const uint32_t qn = min(T.qn, kStageQ), fn = min(T.fn, kStageF), tn = min(T.tn, kStageT);
-    T.qn = qn;
-    T.fn = fn;
+    const uint32_t tn = min(T.tn, kStageT);
     T.tn = tn;
-    T.qbase = qn ? atomicAdd(R.qcnt_out, qn) : 0;
-    T.fbase = fn ? atomicAdd(R.first_cnt, fn) : 0;
     T.tbase = tn ? atomicAdd(R.tcnt, tn) : 0;
   }
   __syncthreads();
-  for (uint32_t i = threadIdx.x; i < T.qn; i += blockDim.x) __stcg(&R.qout[T.qbase + i], T.qbuf[i]);
-  for (uint32_t i = threadIdx.x; i < T.fn; i += blockDim.x) __stcg(&R.first_list[T.fbase + i], T.fbuf[i]);
   for (uint32_t i = threadIdx.x; i < T.tn; i += blockDim.x) tasks[T.tbase + i] = T.tbuf[i];
   __syncthreads();
-  if (threadIdx.x == 0) T.qn = T.fn = T.tn = 0;
+  if (threadIdx.x == 0) T.tn = 0;
 }
 
 // Cut the window [b, b + len) of vertex u into kTaskLen-entry tasks, staged in
@@ -352,25 +359,18 @@ __device__ __forceinline__ void emit_tasks(const KArgs& A, const RoundCtx& R, St
 // Successful relaxation of v to nd (old = previous distance): SAP into the
 // next frontier, first insertion into the settled (or first-step) list, and
 // in the first step the running min over high-degree vertices that becomes
-// ub (Algorithm 1). Warp-collective: every lane calls it. With a stage the
-// appends go through shared memory.
+// ub (Algorithm 1). Warp-collective: every lane calls it; the appends go
+// through the warp's stages.
 __device__ __forceinline__ void on_success(const KArgs& A, const RoundCtx& R, bool ok, uint32_t v, uint32_t nd,
-                                           uint32_t old, Counters& C, Stage* T = nullptr) {
+                                           uint32_t old, Counters& C, WarpList& Q, WarpList& F) {
   bool sap = false;
   if (ok) {
     const uint32_t bit = 1u << (v & 31);
     sap = !(atomicOr(&R.fbits[v >> 5], bit) & bit);
   }
   const bool first = ok && old == EIC_INF;
-  if (T) {
-    staged_append(sap, v, &T->qn, T->qbuf, kStageQ, R.qcnt_out, R.qout);
-    staged_append(first, v, &T->fn, T->fbuf, kStageF, R.first_cnt, R.first_list);
-  } else {
-    const uint32_t slot = warp_append(sap, R.qcnt_out);
-    if (sap) __stcg(&R.qout[slot], v);
-    const uint32_t slot2 = warp_append(first, R.first_cnt);
-    if (first) __stcg(&R.first_list[slot2], v);
-  }
+  warp_push(Q, sap, v);
+  warp_push(F, first, v);
   if (R.step1 && ok) {
     const uint32_t dg = __ldg(&A.G.row[v + 1]) - __ldg(&A.G.row[v]);
     if (dg >= A.G.highd0) atomicMin(&A.ctl->ub_cand, nd);
@@ -394,6 +394,8 @@ __device__ void round_phase(const KArgs& A, const RoundCtx& R, const Local& L, R
   const uint32_t gwarp = qblock(A) * (nt >> 5) + warp, nwarps = A.nb * (nt >> 5);
   const int64_t pull_bound = R.ub - R.st;
   WarpScr& W = S.w[warp];
+  WarpList Qw = {T.wq[warp], 0u, R.qcnt_out, R.qout};
+  WarpList Fw = {T.wf[warp], 0u, R.first_cnt, R.first_list};
   // an item's record: the vertex (frontier, source), {dist, row begin, row
   // end} (push set, from the settled list) or the pull-list entry. The next
   // iteration's record is loaded while this iteration runs.
@@ -559,7 +561,7 @@ __device__ void round_phase(const KArgs& A, const RoundCtx& R, const Local& L, R
             atomicMin(&W.val[lo], (uint32_t)(dvv + ent.y));
         }
       }
-      on_success(A, R, ok, v, nd, old, C, &T);
+      on_success(A, R, ok, v, nd, old, C, Qw, Fw);
     }
     __syncwarp();
     bool pok = false;
@@ -569,9 +571,11 @@ __device__ void round_phase(const KArgs& A, const RoundCtx& R, const Local& L, R
       pold = atomicMin(&A.dist[u], pbest);
       pok = pbest < pold;
     }
-    on_success(A, R, pok, u, pbest, pold, C, &T);
+    on_success(A, R, pok, u, pbest, pold, C, Qw, Fw);
     __syncwarp();
   }
+  warp_flush(Qw);
+  warp_flush(Fw);
   tl_block(A, 6, R.rid);
   stage_flush(T, R, A.tasks);
 }
@@ -581,6 +585,8 @@ __device__ void task_phase(const KArgs& A, const RoundCtx& R, uint32_t ntasks, S
   const uint32_t lane = lane_id();
   const uint32_t wpb = blockDim.x >> 5;
   const uint32_t nwarps = A.nb * wpb;
+  WarpList Qw = {T.wq[threadIdx.x >> 5], 0u, R.qcnt_out, R.qout};
+  WarpList Fw = {T.wf[threadIdx.x >> 5], 0u, R.first_cnt, R.first_list};
   const int64_t pull_bound = R.ub - R.st;
   for (uint32_t t = qblock(A) * wpb + (threadIdx.x >> 5); t < ntasks; t += nwarps) {
     const uint4 tv = ld_list4(&A.tasks[t]);
@@ -602,7 +608,7 @@ __device__ void task_phase(const KArgs& A, const RoundCtx& R, uint32_t ntasks, S
             ok = nd < old;
           }
         }
-        on_success(A, R, ok, v, nd, old, C, &T);
+        on_success(A, R, ok, v, nd, old, C, Qw, Fw);
       }
     } else {  // pull request over a row segment
       uint32_t best = EIC_INF;
@@ -628,9 +634,11 @@ __device__ void task_phase(const KArgs& A, const RoundCtx& R, uint32_t ntasks, S
         old = atomicMin(&A.dist[tk.u], best);
         ok = best < old;
       }
-      on_success(A, R, ok, tk.u, best, old, C, &T);
+      on_success(A, R, ok, tk.u, best, old, C, Qw, Fw);
     }
   }
+  warp_flush(Qw);
+  warp_flush(Fw);
   tl_block(A, 7, R.rid);
   stage_flush(T, R, A.tasks);
 }
@@ -945,7 +953,7 @@ __device__ void run_query(const KArgs& A, QueryShared& Q, uint32_t& gen) {
   L.cur_cnt = 1;  // the first round's frontier is {s}
   Counters C = {0, 0, 0, 0, 0, 0};
   if (threadIdx.x == 0) {
-    T.qn = T.fn = T.tn = 0;
+    T.tn = 0;
     B.st0 = -1;
     B.st1 = -1;
     B.gap_lb = __ldcg(&c->gap_lb);
