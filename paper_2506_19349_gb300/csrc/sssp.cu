@@ -97,6 +97,7 @@ constexpr uint32_t kMaxWarps = kMaxBlock / 32;
 constexpr uint32_t kTaskLen = 64;     // adjacency entries per grid task
 constexpr uint32_t kCursorMin = 16;   // rows longer than this keep a window cursor
 constexpr uint32_t kPullFast = 4;     // pull prefixes shorter than this are answered by their lane
+constexpr uint32_t kSweepNum = 1, kSweepDen = 2;  // sweep the pull set when it holds >= 1/2 of the vertices
 constexpr uint32_t kStageT = 1024;    // tasks staged per block
 constexpr uint32_t kWarpStage = 256;  // next-frontier / settled-list appends staged per warp
 
@@ -174,7 +175,7 @@ union PhaseScr {
 struct Local {
   int64_t lb, ub, st, lb0;
   uint32_t step, rid, qsel, cur_cnt, s_int;
-  uint32_t push_beg, push_end, pull_on, pull_cnt, extra_s, step_off_cur, done;
+  uint32_t push_beg, push_end, pull_on, pull_cnt, pull_sweep, extra_s, step_off_cur, done;
 };
 
 // State of the step controller, kept in block 0's shared memory across steps.
@@ -408,6 +409,7 @@ __device__ void round_phase(const KArgs& A, const RoundCtx& R, const Local& L, R
       const uint2 rr = ld_list2(&A.srow[idx]);
       return make_uint4(ld_list(&A.sd[idx]), rr.x, rr.y, 0u);
     }
+    if (L.pull_sweep) return make_uint4(ii - np, 0u, 0u, 0u);  // every vertex, in id order
     return ld_stream4(&A.G.nz[ii - np]);
   };
   uint4 pre = fetch(gwarp * 32 + lane);
@@ -453,21 +455,24 @@ __device__ void round_phase(const KArgs& A, const RoundCtx& R, const Local& L, R
           }
         }
       } else {  // pull set: unsettled, smallest weight < ub - st (Function 1)
-        const uint4 z = rec;
+        uint4 z = rec;  // {vertex, lightest weight, row begin, row end}
         u = z.x;
         mode = kModePull;
-        // the settled bit and the row's first kPullFast entries, loaded together
-        const uint32_t rl = z.w - z.z;
         const uint32_t bits = __ldcg(&A.sbits[u >> 5]);
         if (!((bits >> (u & 31)) & 1u)) {  // unsettled: its row's first kPullFast entries, together
+          if (L.pull_sweep) {
+            z.z = __ldg(&A.G.row[u]);
+            z.w = __ldg(&A.G.row[u + 1]);
+          }
+          const uint32_t rl = z.w - z.z;
           uint2 ent[kPullFast];
 #pragma unroll
           for (uint32_t k = 0; k < kPullFast; ++k)
             ent[k] = k < rl ? ld_stream(&A.G.adj[z.z + k]) : make_uint2(0u, EIC_INF);
-          C.pitems += 1;
-          uint32_t c = 0;  // the prefix with w < ub - st (rows are weight-sorted; the first entry is in it)
+          uint32_t c = 0;  // the prefix with w < ub - st (rows are weight-sorted)
 #pragma unroll
           for (uint32_t k = 0; k < kPullFast; ++k) c += (k < rl && (int64_t)ent[k].y < pull_bound) ? 1u : 0u;
+          C.pitems += c > 0 ? 1 : 0;  // in the pull set iff its lightest edge is below the bound
           plong = c == kPullFast && rl > kPullFast;  // the prefix goes on: the warp scans the rest
           {  // the loaded part of the prefix, answered in the lane
             uint32_t dv[kPullFast];
@@ -863,7 +868,13 @@ __device__ void step_boundary(const KArgs& A, PhaseScr& P, BState& B, const Loca
     c->push_beg = pb;
     c->push_end = pe;
     c->pull_on = pull_on;
-    c->pull_cnt = pull_cnt;
+    // a pull set of most vertices is swept in vertex order: rows are read in
+    // address order across the grid (the weight-ordered list would make one
+    // pass per weight value), and what the round inserts comes out in
+    // vertex order, which the next round and the statistics pass read
+    const uint32_t sweep = pull_on && (uint64_t)pull_cnt * kSweepDen >= (uint64_t)G.ni * kSweepNum ? 1u : 0u;
+    c->pull_sweep = sweep;
+    c->pull_cnt = sweep ? G.ni : pull_cnt;
     c->extra_s = extra;
     c->step_off_cur = settled_now;
     B.sumd_lb = sumd_ub;
@@ -893,6 +904,7 @@ __device__ void read_ctl(const Ctl* c, Local& L) {
     sL.push_end = __ldcg(&c->push_end);
     sL.pull_on = __ldcg(&c->pull_on);
     sL.pull_cnt = __ldcg(&c->pull_cnt);
+    sL.pull_sweep = __ldcg(&c->pull_sweep);
     sL.extra_s = __ldcg(&c->extra_s);
     sL.step_off_cur = __ldcg(&c->step_off_cur);
     sL.done = __ldcg(&c->done);
@@ -1200,6 +1212,7 @@ __device__ void ctl_init(const KArgs& A) {
   c->done = si == EIC_INF ? 1u : 0u;
   c->push_beg = c->push_end = 0;
   c->pull_on = c->pull_cnt = c->extra_s = 0;
+  c->pull_sweep = 0;
   c->step_off_cur = 0;
   c->st0 = -1;
   c->st1 = -1;
