@@ -72,8 +72,6 @@ KERNEL_SOURCES = ("paper_2506_19349_gb300/csrc/sssp.cu", "paper_2506_19349_gb300
 MEASURED_TRAFFIC = {  # {(scale, sources sha256): bytes per launch}
     (25, "3e6c8f887587883ed3f68e125e4e8cdffbec7ee50c7d3dac653cd7e1552335e8"): 6462482432,
 }
-    (25, "8fbed50c095342e0b4061c922950897e8750f359ee16f27f89651d8e8cfbc2e6"): 9832430464,
-}
 
 
 def kernel_sources_sha256():
