@@ -45,9 +45,8 @@ struct Ctl {
   uint32_t s2_done;
   uint32_t next_q;  // batch: the query the group's first block claimed
   unsigned long long next_ticket;  // serving: the request the group's first block claimed
-  uint32_t acc_maxd;
+  uint32_t acc_maxd1;  // 1 + the largest distance settled in the step (0: none)
   unsigned long long acc_deg;
-  uint32_t acc_any;
   unsigned long long cnt_rounds, cnt_frontier, cnt_trav, cnt_pulls, cnt_improved, cnt_heavy, cnt_pitems;
   GridBarrier bar;
   int status;

@@ -185,8 +185,8 @@ struct BState {
   uint32_t j0;
 };
 
-struct Counters {
-  unsigned long long frontier, trav, pulls, improved, heavy, pitems;
+struct Counters {  // one thread's counts over the query (added to the 64-bit totals at its end)
+  uint32_t frontier, trav, pulls, improved, heavy, pitems;
 };
 
 __device__ __forceinline__ void tl_mark(const KArgs& A, uint32_t kind, uint32_t rid) {
@@ -741,11 +741,11 @@ __device__ void step_boundary(const KArgs& A, PhaseScr& P, BState& B, const Loca
   if (threadIdx.x == 0) {
     const uint32_t settled_now = __ldcg(&c->settled_cnt);
     const unsigned long long acc = __ldcg(&c->acc_deg);
-    const uint32_t acc_any = __ldcg(&c->acc_any), acc_maxd = __ldcg(&c->acc_maxd);
+    const uint32_t acc_maxd1 = __ldcg(&c->acc_maxd1);
     const uint64_t sumd_ub = B.sumd_lb - acc;
     sh_u[0] = sumd_ub;
     sh_u[1] = settled_now;
-    if (acc_any && (int64_t)acc_maxd > B.max_settled) B.max_settled = acc_maxd;
+    if (acc_maxd1 && (int64_t)(acc_maxd1 - 1) > B.max_settled) B.max_settled = acc_maxd1 - 1;
     const int64_t maxs = B.max_settled;
     A.step_ub[k] = ub;
     if (k <= A.trace_cap && A.trace) {
@@ -777,7 +777,17 @@ __device__ void step_boundary(const KArgs& A, PhaseScr& P, BState& B, const Loca
   }
   __syncthreads();
   const uint64_t sumd_ub = sh_u[0];
-  const uint32_t highd_ub = block_highd(A.hist, G.dvals, G.D);
+  uint32_t highd_ub;
+  if (G.D <= 32 * kWarpHighdPer) {  // one warp, no block barriers
+    if (threadIdx.x < 32) {
+      const uint32_t h = warp_highd(A.hist, G.dvals, G.D);
+      if (threadIdx.x == 0) sh_flag[1] = h;
+    }
+    __syncthreads();
+    highd_ub = sh_flag[1];
+  } else {
+    highd_ub = block_highd(A.hist, G.dvals, G.D);
+  }
   if (sh_flag[0]) {
     if (threadIdx.x == 0) {
       c->done = 1;
@@ -881,8 +891,7 @@ __device__ void step_boundary(const KArgs& A, PhaseScr& P, BState& B, const Loca
     B.highd_lb = highd_ub;
     B.gap_lb = gap_raw;
     c->acc_deg = 0;
-    c->acc_maxd = 0;
-    c->acc_any = 0;
+    c->acc_maxd1 = 0;
     c->s2_done = 0;
     c->done = 0;
     __threadfence();
@@ -1062,18 +1071,21 @@ __device__ void run_query(const KArgs& A, QueryShared& Q, uint32_t& gen) {
     // ------------------------------------------------ statistics pass
     {
       S2Scr& S = P.s2;
-      for (int r = threadIdx.x; r < kShRanks; r += blockDim.x) S.hist[r] = 0;
-      const int64_t wlo = L.ub - (int64_t)A.G.maxw > L.lb ? L.ub - (int64_t)A.G.maxw : L.lb;
-      const bool ring_sh = A.ring_shift == 0 && L.ub < EIC_INF_T && (L.ub - wlo) <= kShRing;
-      if (ring_sh)
-        for (int r = threadIdx.x; r < kShRing; r += blockDim.x) S.ring[r] = 0;
-      __syncthreads();
       const bool step1 = L.step == 1;
       const uint32_t* list = step1 ? A.touched : A.sid;
       const uint32_t lbeg = step1 ? 0 : L.step_off_cur;
       if (threadIdx.x == 0) sh_snap[3] = step1 ? __ldcg(&c->touched_cnt) : __ldcg(&c->settled_cnt);
       __syncthreads();
       const uint32_t lend = (uint32_t)sh_snap[3];
+      const bool has = lbeg + qb * blockDim.x < lend;  // this block has settled vertices to count
+      const int64_t wlo = L.ub - (int64_t)A.G.maxw > L.lb ? L.ub - (int64_t)A.G.maxw : L.lb;
+      const bool ring_sh = A.ring_shift == 0 && L.ub < EIC_INF_T && (L.ub - wlo) <= kShRing;
+      if (has) {
+        for (int r = threadIdx.x; r < kShRanks; r += blockDim.x) S.hist[r] = 0;
+        if (ring_sh)
+          for (int r = threadIdx.x; r < kShRing; r += blockDim.x) S.ring[r] = 0;
+      }
+      __syncthreads();
       unsigned long long bdeg = 0;
       uint32_t bmax = 0, bany = 0;
       const uint32_t nthreads = A.nb * blockDim.x;
@@ -1128,30 +1140,29 @@ __device__ void run_query(const KArgs& A, QueryShared& Q, uint32_t& gen) {
         }
       }
       __syncthreads();
-      for (int r = threadIdx.x; r < kShRanks; r += blockDim.x)
-        if (S.hist[r]) atomicSub(&A.hist[r], S.hist[r]);
-      if (ring_sh)
-        for (int r = threadIdx.x; r < kShRing && r < L.ub - wlo; r += blockDim.x)
-          if (S.ring[r]) atomicAdd(&A.ring[((uint64_t)(wlo + r)) & A.ring_mask], S.ring[r]);
-      for (int o = 16; o > 0; o >>= 1) {
-        bmax = max(bmax, __shfl_xor_sync(EIC_FULL_MASK, bmax, o));
-        bany |= __shfl_xor_sync(EIC_FULL_MASK, bany, o);
+      if (has) {
+        for (int r = threadIdx.x; r < kShRanks; r += blockDim.x)
+          if (S.hist[r]) atomicSub(&A.hist[r], S.hist[r]);
+        if (ring_sh)
+          for (int r = threadIdx.x; r < kShRing && r < L.ub - wlo; r += blockDim.x)
+            if (S.ring[r]) atomicAdd(&A.ring[((uint64_t)(wlo + r)) & A.ring_mask], S.ring[r]);
       }
-      if ((threadIdx.x & 31) == 0 && bany) {
-        atomicMax(&c->acc_maxd, bmax);
-        atomicOr(&c->acc_any, 1u);
+      // block totals: degree sum and 1 + the largest distance (0: none), one atomic each
+      unsigned long long v[2] = {bdeg, bany ? (unsigned long long)bmax + 1 : 0ull};
+      v[0] = warp_sum_u64(v[0]);
+      for (int o = 16; o > 0; o >>= 1) v[1] = max(v[1], __shfl_xor_sync(EIC_FULL_MASK, v[1], o));
+      if ((threadIdx.x & 31) == 0) {
+        sh_red[threadIdx.x >> 5][0] = v[0];
+        sh_red[threadIdx.x >> 5][1] = v[1];
       }
-      unsigned long long v[7] = {bdeg, C.frontier, C.trav, C.pulls, C.improved, C.heavy, C.pitems};
-      block_sums<7>(v, sh_red);
-      C = {0, 0, 0, 0, 0, 0};
+      __syncthreads();
       if (threadIdx.x == 0) {
+        for (uint32_t w = 1; w < (blockDim.x >> 5); ++w) {
+          v[0] += sh_red[w][0];
+          v[1] = max(v[1], sh_red[w][1]);
+        }
         if (v[0]) atomicAdd(&c->acc_deg, v[0]);
-        atomicAdd(&c->cnt_frontier, v[1]);
-        atomicAdd(&c->cnt_trav, v[2]);
-        atomicAdd(&c->cnt_pulls, v[3]);
-        atomicAdd(&c->cnt_improved, v[4]);
-        atomicAdd(&c->cnt_heavy, v[5]);
-        atomicAdd(&c->cnt_pitems, v[6]);
+        if (v[1]) atomicMax(&c->acc_maxd1, (uint32_t)v[1]);
         __threadfence();
         atomicAdd(&c->s2_done, 1u);
       }
@@ -1178,6 +1189,18 @@ __device__ void run_query(const KArgs& A, QueryShared& Q, uint32_t& gen) {
     if (qb == 0 && threadIdx.x == 0) tl_mark(A, 3, L.rid);
     read_ctl(c, L);
     if (L.done) break;
+  }
+  {  // the query's counters, once per block
+    unsigned long long v[7] = {C.frontier, C.trav, C.pulls, C.improved, C.heavy, C.pitems, 0ull};
+    block_sums<7>(v, sh_red);
+    if (threadIdx.x == 0) {
+      atomicAdd(&c->cnt_frontier, v[0]);
+      atomicAdd(&c->cnt_trav, v[1]);
+      atomicAdd(&c->cnt_pulls, v[2]);
+      atomicAdd(&c->cnt_improved, v[3]);
+      atomicAdd(&c->cnt_heavy, v[4]);
+      atomicAdd(&c->cnt_pitems, v[5]);
+    }
   }
   if (qb == 0 && threadIdx.x == 0 && A.status_out) *A.status_out = ld_volatile_int(&c->status);
 }
@@ -1230,9 +1253,8 @@ __device__ void ctl_init(const KArgs& A) {
   c->ub_cand = (G.highd0 > 0 && dgs >= G.highd0) ? 0u : EIC_INF;
   c->tcnt[0] = c->tcnt[1] = c->tcnt[2] = 0;
   c->s2_done = 0;
-  c->acc_maxd = 0;
+  c->acc_maxd1 = 0;
   c->acc_deg = 0;
-  c->acc_any = 0;
   c->cnt_rounds = c->cnt_frontier = c->cnt_trav = c->cnt_pulls = c->cnt_improved = c->cnt_heavy = 0;
   c->cnt_pitems = 0;
 }

@@ -85,6 +85,49 @@ static __device__ uint32_t block_highd(const uint32_t* cnt, const uint32_t* dval
   return res;
 }
 
+// The same for D <= 32 * kWarpHighdPer distinct degrees by one warp (no block
+// barriers): lane l holds a contiguous run of ranks, a shuffle scan gives each
+// run's starting total, and a shuffle arg-min picks the rank (ties: smaller
+// rank). Called by the 32 lanes of one warp; every lane gets the result.
+constexpr uint32_t kWarpHighdPer = 32;
+static __device__ uint32_t warp_highd(const uint32_t* cnt, const uint32_t* dvals, uint32_t D) {
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint32_t per = (D + 31) / 32;
+  const uint32_t lo = min(D, lane * per), hi = min(D, lo + per);
+  uint64_t sum = 0;
+  for (uint32_t r = lo; r < hi; ++r) sum += (uint64_t)__ldcg(&cnt[r]) * dvals[r];
+  uint64_t incl = sum;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint64_t y = __shfl_up_sync(EIC_FULL_MASK, incl, o);
+    if ((int)lane >= o) incl += y;
+  }
+  const uint64_t total = __shfl_sync(EIC_FULL_MASK, incl, 31);
+  uint64_t low = incl - sum;
+  uint64_t bdiff = UINT64_MAX;
+  uint32_t brank = UINT32_MAX;
+  for (uint32_t r = lo; r < hi; ++r) {
+    const uint32_t c = __ldcg(&cnt[r]);
+    if (c == 0) continue;
+    const uint64_t high = total - low;
+    const uint64_t diff = high > low ? high - low : low - high;
+    if (diff < bdiff) {
+      bdiff = diff;
+      brank = r;
+    }
+    low += (uint64_t)c * dvals[r];
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    const uint64_t od = __shfl_xor_sync(EIC_FULL_MASK, bdiff, o);
+    const uint32_t orr = __shfl_xor_sync(EIC_FULL_MASK, brank, o);
+    if (od < bdiff || (od == bdiff && orr < brank)) {
+      bdiff = od;
+      brank = orr;
+    }
+  }
+  return (total == 0 || brank == UINT32_MAX) ? 0u : dvals[brank];
+}
+
 // Eq. 1-3. maxW(G, ratio) is read from RtoW at index floor(ratio * (R - 1));
 // Eq. 2 is evaluated as -expm1(log1p(-prob) / (prob * highD)). Every
 // operation is an explicitly rounded IEEE double operation (no contraction).
