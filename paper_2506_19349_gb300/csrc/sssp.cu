@@ -409,7 +409,10 @@ __device__ void round_phase(const KArgs& A, const RoundCtx& R, const Local& L, R
       const uint2 rr = ld_list2(&A.srow[idx]);
       return make_uint4(ld_list(&A.sd[idx]), rr.x, rr.y, 0u);
     }
-    if (L.pull_sweep) return make_uint4(ii - np, 0u, 0u, 0u);  // every vertex, in id order
+    if (L.pull_sweep) {  // every vertex in id order: {vertex, settled word, row begin, row end}
+      const uint32_t v = ii - np;
+      return make_uint4(v, __ldcg(&A.sbits[v >> 5]), __ldg(&A.G.row[v]), __ldg(&A.G.row[v + 1]));
+    }
     return ld_stream4(&A.G.nz[ii - np]);
   };
   uint4 pre = fetch(gwarp * 32 + lane);
@@ -455,15 +458,11 @@ __device__ void round_phase(const KArgs& A, const RoundCtx& R, const Local& L, R
           }
         }
       } else {  // pull set: unsettled, smallest weight < ub - st (Function 1)
-        uint4 z = rec;  // {vertex, lightest weight, row begin, row end}
+        const uint4 z = rec;  // {vertex, lightest weight or settled word, row begin, row end}
         u = z.x;
         mode = kModePull;
-        const uint32_t bits = __ldcg(&A.sbits[u >> 5]);
+        const uint32_t bits = L.pull_sweep ? z.y : __ldcg(&A.sbits[u >> 5]);
         if (!((bits >> (u & 31)) & 1u)) {  // unsettled: its row's first kPullFast entries, together
-          if (L.pull_sweep) {
-            z.z = __ldg(&A.G.row[u]);
-            z.w = __ldg(&A.G.row[u + 1]);
-          }
           const uint32_t rl = z.w - z.z;
           uint2 ent[kPullFast];
 #pragma unroll
