@@ -387,6 +387,9 @@ def serving(eic, torch, stream, rates, seconds_per_rate, max_per_rate):
     plain_qps = 1000.0 / statistics.mean(svc)
     del dist
     srv = eic.Server(graphs)
+    t0 = time.perf_counter()
+    shifts = srv.tune([pools[g][0] for g in range(len(graphs))])  # per-graph step width (exact)
+    tune_s = time.perf_counter() - t0
     rows = []
     rng = np.random.default_rng(11)
     switch = sys.getswitchinterval()
@@ -450,6 +453,7 @@ def serving(eic, torch, stream, rates, seconds_per_rate, max_per_rate):
     return {"workload": "resident RMAT scales 18,19,20,21,22,22,23 and a 2048^2 grid (weights [1,255]); requests "
                         "(graph, source) uniform over 32 sources per graph, Poisson arrivals",
             "generate_s": gen_s, "groups": info["groups"], "blocks_per_group": info["blocks_per_group"],
+            "tuned_gap_shift_per_graph": shifts, "tune_s": tune_s,
             "plain_one_at_a_time_qps": plain_qps, "plain_service_ms_mean": statistics.mean(svc),
             "rates": rows, "peak_served_qps": best, "speedup_vs_one_at_a_time": best / plain_qps,
             "latency": "submit to completion seen by the host runtime; one-at-a-time latencies replay the measured "

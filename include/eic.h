@@ -306,6 +306,16 @@ int eic_batch_destroy(eic_batch* b);
  * eic_server_release  forgets a done request and frees its result buffer.
  * eic_server_stats    counters and the latency percentiles of the requests
  *                     completed since creation or the last reset.
+ * eic_server_tune     autotuner for the resident graphs: for each graph k it
+ *                     picks the step-width scaling (gap_shift, exact for every
+ *                     value) that runs sample_sources[k] fastest in one of the
+ *                     server's block groups, trying params->gap_shift + 0, 1,
+ *                     2, ... while the time falls by 2% (up to 8); one copy of
+ *                     the sample runs per group and each setting is timed
+ *                     twice. gap_shifts (host array of num_graphs, or NULL)
+ *                     receives the choices. The server must be idle (nothing
+ *                     queued or in flight: EIC_EBUSY otherwise); submissions
+ *                     wait until it returns. Synchronous.
  * eic_server_destroy  stops the kernel and the pump; pending requests are
  *                     dropped. NULL accepted.
  */
@@ -338,6 +348,7 @@ int eic_server_result(eic_server* s, uint64_t ticket, uint32_t* host_dist, const
 int eic_server_release(eic_server* s, uint64_t ticket);
 int eic_server_stats(eic_server* s, eic_server_report* out);
 int eic_server_reset_stats(eic_server* s);
+int eic_server_tune(eic_server* s, const uint32_t* sample_sources, uint32_t* gap_shifts);
 int eic_server_destroy(eic_server* s);
 
 /*

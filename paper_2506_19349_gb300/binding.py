@@ -28,7 +28,7 @@ EXPORTS = ("eic_params_default", "eic_strerror", "eic_version", "eic_graph_creat
            "eic_sssp_noalloc", "eic_batch_create", "eic_batch_run", "eic_batch_wait", "eic_batch_tune",
            "eic_batch_info", "eic_batch_destroy", "eic_server_create", "eic_server_submit", "eic_server_poll",
            "eic_server_wait", "eic_server_result", "eic_server_release", "eic_server_stats",
-           "eic_server_reset_stats", "eic_server_destroy")
+           "eic_server_reset_stats", "eic_server_tune", "eic_server_destroy")
 
 
 class Params(ctypes.Structure):
@@ -147,6 +147,8 @@ def load_library(path: str | None = None):
         L.eic_server_stats.restype = c_int
         L.eic_server_reset_stats.argtypes = [vp]
         L.eic_server_reset_stats.restype = c_int
+        L.eic_server_tune.argtypes = [vp, vp, vp]
+        L.eic_server_tune.restype = c_int
         L.eic_server_destroy.argtypes = [vp]
         L.eic_server_destroy.restype = c_int
         _lib = L
@@ -410,6 +412,16 @@ class Server:
 
     def reset_stats(self):
         _check(load_library().eic_server_reset_stats(self._h), "eic_server_reset_stats")
+
+    def tune(self, sample_sources) -> list:
+        """Per resident graph, the step-width scaling that serves its sample
+        source fastest (eic_server_tune); returns the chosen values."""
+        src = np.ascontiguousarray(sample_sources, dtype=np.uint32)
+        if src.size != len(self._graphs):
+            raise ValueError("one sample source per resident graph")
+        out = np.zeros(src.size, dtype=np.uint32)
+        _check(load_library().eic_server_tune(self._h, src.ctypes.data, out.ctypes.data), "eic_server_tune")
+        return out.tolist()
 
     def close(self):
         if getattr(self, "_h", None) and self._h.value and _lib is not None:

@@ -59,6 +59,7 @@ struct BatchQuery {
   uint32_t* out;
   uint32_t s;
   uint32_t ring_mask, ring_shift, task_cap;
+  uint32_t gap_shift, heavy_min;  // step-width scaling and window-class threshold for this query's graph
 };
 
 // Scratch of one block group, reused by every query the group runs.

@@ -116,6 +116,7 @@ struct Request {
 struct eic_server {
   int device = 0;
   std::vector<const eic_graph*> graphs;
+  std::vector<BatchQuery> hq;  // the resident graphs' table (host copy of d_graphs)
   BatchQuery* d_graphs = nullptr;
   eic_params p{};
   uint32_t groups = 0, nb = 0, block = 0, cap = 0;
@@ -347,6 +348,8 @@ int eic_server_create(const eic_graph* const* graphs, uint32_t num_graphs, const
     q.ring_mask = (1u << bits) - 1u;
     q.ring_shift = shift;
     q.task_cap = (uint32_t)(G.two_m / kHeavyMinFloor + 2);
+    q.gap_shift = pr.gap_shift;
+    q.heavy_min = pr.heavy_min;
     hq.push_back(q);
     caps.ni = std::max<uint64_t>(caps.ni, G.ni);
     caps.two_m = std::max<uint64_t>(caps.two_m, G.two_m);
@@ -399,6 +402,7 @@ int eic_server_create(const eic_graph* const* graphs, uint32_t num_graphs, const
     rc = EIC_ENOMEM;
     goto fail;
   }
+  s->hq = hq;
   s->entry_ticket.assign(s->cap, kNone);
   s->pump = std::thread([s] { s->pump_loop(); });
   cudaSetDevice(prev);
@@ -534,6 +538,39 @@ int eic_server_reset_stats(eic_server* s) {
   s->lat_ms.clear();
   s->max_inflight = s->admitted.size();
   return EIC_OK;
+}
+
+int eic_server_tune(eic_server* s, const uint32_t* sample_sources, uint32_t* gap_shifts) {
+  if (!s || !sample_sources) return EIC_EINVAL;
+  for (size_t k = 0; k < s->graphs.size(); ++k)
+    if (sample_sources[k] >= s->graphs[k]->dg.n) return EIC_EINVAL;
+  int prev = 0;
+  cudaGetDevice(&prev);
+  cudaSetDevice(s->device);
+  std::unique_lock<std::mutex> lk(s->mu);  // submissions wait while the server tunes
+  if (!s->queue.empty() || !s->admitted.empty()) {
+    cudaSetDevice(prev);
+    return EIC_EBUSY;
+  }
+  // let a resident serving kernel leave before timing other launches
+  if (s->running && cudaStreamSynchronize(s->kstream) != cudaSuccess) (void)cudaGetLastError();
+  s->running = false;
+  int rc = EIC_OK;
+  for (size_t k = 0; k < s->graphs.size() && rc == EIC_OK; ++k) {
+    uint32_t best = s->p.gap_shift;
+    double ms = 0;
+    rc = eic_tune_step_width(s->graphs[k], sample_sources[k], s->groups, s->nb, s->p, s->p.gap_shift, s->cstream,
+                             &best, &ms);
+    if (rc == EIC_OK) s->hq[k].gap_shift = best;
+    if (gap_shifts) gap_shifts[k] = s->hq[k].gap_shift;
+  }
+  if (rc == EIC_OK && cudaMemcpy(s->d_graphs, s->hq.data(), s->hq.size() * sizeof(BatchQuery),
+                                 cudaMemcpyHostToDevice) != cudaSuccess) {
+    (void)cudaGetLastError();
+    rc = EIC_ECUDA;
+  }
+  cudaSetDevice(prev);
+  return rc;
 }
 
 int eic_server_destroy(eic_server* s) {

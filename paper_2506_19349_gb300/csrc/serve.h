@@ -61,3 +61,10 @@ int eic_serve_launch(const ServeArgs& args, uint32_t groups, uint32_t block, cud
 
 // Co-resident blocks of the serving kernel at this block size.
 int eic_serve_grid(int block, uint32_t* grid);
+
+// The step-width scaling (gap_shift, from `from` upwards while it helps by 2%,
+// up to 8) that runs (g, source) fastest in a group of nb blocks: `copies`
+// copies run at once, one per group, and each setting is timed twice on
+// stream (the faster kept). *best_ms receives that setting's time.
+int eic_tune_step_width(const eic_graph* g, uint32_t source, uint32_t copies, uint32_t nb, const eic_params& p,
+                        uint32_t from, cudaStream_t stream, uint32_t* best_shift, double* best_ms);

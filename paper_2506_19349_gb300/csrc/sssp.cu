@@ -1392,8 +1392,8 @@ __global__ void __launch_bounds__(kMaxBlock, 2) k_eic_batch(BatchArgs P) {
       sA.alpha = P.alpha;
       sA.beta = P.beta;
       sA.st_num = P.st_num;
-      sA.gap_shift = P.gap_shift;
-      sA.heavy_min = P.heavy_min;
+      sA.gap_shift = bq.gap_shift;
+      sA.heavy_min = bq.heavy_min;
       sA.max_spin = P.max_spin;
       sA.flags = P.flags;
       sA.ring_mask = bq.ring_mask;
@@ -1570,8 +1570,8 @@ __global__ void __launch_bounds__(kMaxBlock, 2) k_eic_serve(ServeArgs P) {
       sA.alpha = P.alpha;
       sA.beta = P.beta;
       sA.st_num = P.st_num;
-      sA.gap_shift = P.gap_shift;
-      sA.heavy_min = P.heavy_min;
+      sA.gap_shift = bq.gap_shift;
+      sA.heavy_min = bq.heavy_min;
       sA.max_spin = P.max_spin;
       sA.flags = P.flags;
       sA.ring_mask = bq.ring_mask;
@@ -1955,6 +1955,9 @@ struct eic_batch {
   uint32_t nq = 0;
   eic_params p{};
   std::vector<uint32_t> order;  // claim position -> caller's query index
+  std::vector<const eic_graph*> qgraph;  // claim position -> graph, source, output
+  std::vector<uint32_t> qsource;
+  std::vector<uint32_t*> qdist;
   std::vector<BatchQuery> hq;
   struct Trivial {
     uint32_t* dist;
@@ -1990,11 +1993,17 @@ uint32_t groups_that_fit(eic_batch* b, uint32_t want) {
   return (uint32_t)(fit < want ? fit : want);
 }
 
-// groups -> blocks per group for the current block shape.
-int batch_configure(eic_batch* b, uint32_t groups, uint32_t block) {
+// groups -> blocks per group for the current block shape; nb_force (when
+// nonzero) fixes the blocks per group instead, and the groups then fill at
+// most the co-resident grid.
+int batch_configure(eic_batch* b, uint32_t groups, uint32_t block, uint32_t nb_force = 0) {
   uint32_t gmax = 0;
   int rc = batch_grid((int)block, &gmax);
   if (rc) return rc;
+  if (nb_force) {
+    if (nb_force > gmax) nb_force = gmax;
+    if (groups == 0 || groups > gmax / nb_force) groups = gmax / nb_force;
+  }
   const uint32_t nrun = (uint32_t)b->hq.size();
   if (groups == 0) {  // library choice: about 8 blocks per group, more for graphs above 2^27 entries
     const uint64_t per = b->caps.two_m >> 24;
@@ -2013,7 +2022,18 @@ int batch_configure(eic_batch* b, uint32_t groups, uint32_t block) {
   b->groups = groups;
   b->block = block;
   b->grid_max = gmax;
-  b->nb = gmax / groups;
+  b->nb = nb_force ? nb_force : gmax / groups;
+  return EIC_OK;
+}
+
+// The host query table to the device (per-query parameters changed).
+int batch_upload(eic_batch* b) {
+  if (b->hq.empty()) return EIC_OK;
+  EIC_CUDA_TRY(cudaMemcpy(b->d_q, b->hq.data(), b->hq.size() * sizeof(BatchQuery), cudaMemcpyHostToDevice));
+  if (b->exec) {
+    cudaGraphExecDestroy(b->exec);
+    b->exec = nullptr;
+  }
   return EIC_OK;
 }
 
@@ -2105,8 +2125,13 @@ int batch_create(const eic_graph* const* graphs, const uint32_t* sources, uint32
     q.ring_mask = (1u << bits) - 1u;
     q.ring_shift = shift;
     q.task_cap = (uint32_t)(G.two_m / kHeavyMinFloor + 2);
+    q.gap_shift = p.gap_shift;
+    q.heavy_min = p.heavy_min;
     b->hq.push_back(q);
     b->order.push_back(i);
+    b->qgraph.push_back(graphs[i]);
+    b->qsource.push_back(sources[i]);
+    b->qdist.push_back(dists[i]);
     SlotCaps& c = b->caps;
     c.ni = G.ni > c.ni ? G.ni : c.ni;
     c.two_m = G.two_m > c.two_m ? G.two_m : c.two_m;
@@ -2262,15 +2287,17 @@ int eic_batch_tune(eic_batch* b, void* stream, eic_batch_config* best) {
   cudaStream_t st = (cudaStream_t)stream;
   if (!b->hq.empty()) {
     const uint32_t nrun = (uint32_t)b->hq.size();
-    uint32_t best_g = b->groups, best_block = b->block;
-    eic_params best_p = b->p;
+    int rc = EIC_OK;
+    uint32_t best_g = b->groups, best_block = b->block, best_hm = b->p.heavy_min;
     double best_ms = 1e300;
     // one configuration: a warm-up run, then a timed one when the warm-up was
-    // within 2x of the best so far; returns the time (or < 0 on error)
-    auto trial = [&](uint32_t g, uint32_t block, const eic_params& pp, double* ms_out) -> int {
-      b->p = pp;
-      int rc = batch_configure(b, g, block);
-      if (rc) return rc;
+    // within 2x of the best so far
+    auto trial = [&](uint32_t g, uint32_t block, uint32_t hm, double* ms_out) -> int {
+      for (auto& q : b->hq) q.heavy_min = hm;
+      b->p.heavy_min = hm;
+      int r = batch_upload(b);
+      if (r) return r;
+      if ((r = batch_configure(b, g, block))) return r;
       double ms = batch_time(b, st);
       if (ms < 0) return EIC_ECUDA;
       if (ms < 2.0 * best_ms) {
@@ -2282,44 +2309,85 @@ int eic_batch_tune(eic_batch* b, void* stream, eic_batch_config* best) {
         best_ms = ms;
         best_g = b->groups;
         best_block = b->block;
-        best_p = pp;
+        best_hm = hm;
       }
       if (ms_out) *ms_out = ms;
       return EIC_OK;
     };
     uint32_t gmax = 0;
-    int rc = batch_grid((int)b->block, &gmax);
-    if (rc) return rc;
+    if ((rc = batch_grid((int)b->block, &gmax))) return rc;
     // pass 1: group counts (divisors of the grid and powers of two), from the
     // most groups down, until two in a row are 20% slower than the best
     std::vector<uint32_t> cand;
     for (uint32_t g = gmax; g >= 1; --g)
       if (g <= nrun && (gmax % g == 0 || (g & (g - 1)) == 0)) cand.push_back(g);
     uint32_t worse = 0;
-    const eic_params base = b->p;
     for (uint32_t g : cand) {
       double ms = 0;
-      if ((rc = trial(g, b->block, base, &ms))) return rc;
+      if ((rc = trial(g, b->block, best_hm, &ms))) return rc;
       worse = ms > 1.2 * best_ms ? worse + 1 : 0;
       if (worse >= 2) break;
     }
-    // pass 2 at the best group count: step-width scaling upwards while it
-    // helps, then the window-class threshold, then a 256-thread block
-    for (uint32_t gs = best_p.gap_shift + 1; gs <= 8; ++gs) {
-      eic_params pp = best_p;
-      pp.gap_shift = gs;
-      const double before = best_ms;
-      if ((rc = trial(best_g, best_block, pp, nullptr))) return rc;
-      if (best_ms >= before) break;
+    // pass 2: each graph's step-width scaling (exact for every value), timed on
+    // a sub-batch of that graph's queries at the chosen blocks per group:
+    // gap_shift + 1, + 2, ... while it helps by 2% (up to 8)
+    if ((rc = batch_configure(b, best_g, best_block))) return rc;
+    const uint32_t nb = b->nb;
+    std::vector<const eic_graph*> seen;
+    for (uint32_t k = 0; k < nrun; ++k) {
+      const eic_graph* g = b->qgraph[k];
+      if (std::find(seen.begin(), seen.end(), g) != seen.end()) continue;
+      seen.push_back(g);
+      std::vector<uint32_t> pos;
+      for (uint32_t j = 0; j < nrun; ++j)
+        if (b->qgraph[j] == g) pos.push_back(j);
+      std::vector<const eic_graph*> sg(pos.size(), g);
+      std::vector<uint32_t> ss;
+      std::vector<uint32_t*> sd;
+      for (uint32_t j : pos) {
+        ss.push_back(b->qsource[j]);
+        sd.push_back(b->qdist[j]);
+      }
+      eic_batch* sub = nullptr;
+      if ((rc = batch_create(sg.data(), ss.data(), (uint32_t)pos.size(), sd.data(), &b->p, nullptr, &sub)))
+        return rc;
+      rc = batch_configure(sub, (uint32_t)pos.size(), best_block, nb);
+      uint32_t gs_best = b->hq[k].gap_shift;
+      double t_best = -1.0;
+      for (uint32_t gs = gs_best; rc == EIC_OK && gs <= 8; ++gs) {
+        for (auto& q : sub->hq) q.gap_shift = gs;
+        if ((rc = batch_upload(sub))) break;
+        double t = batch_time(sub, st);
+        const double t2 = batch_time(sub, st);
+        if (t < 0 || t2 < 0) {
+          rc = EIC_ECUDA;
+          break;
+        }
+        t = t2 < t ? t2 : t;
+        if (t_best < 0 || t < 0.98 * t_best) {
+          t_best = t;
+          gs_best = gs;
+        } else {
+          break;
+        }
+      }
+      batch_free(sub);
+      if (rc) return rc;
+      for (uint32_t j : pos) b->hq[j].gap_shift = gs_best;
     }
-    for (uint32_t hm : {64u, 256u}) {
-      eic_params pp = best_p;
-      pp.heavy_min = hm;
-      if ((rc = trial(best_g, best_block, pp, nullptr))) return rc;
-    }
-    if ((rc = trial(best_g, 256, best_p, nullptr))) return rc;
+    best_ms = 1e300;
+    if ((rc = trial(best_g, best_block, best_hm, nullptr))) return rc;
+    // pass 3 at the best group count: the window-class threshold, then a
+    // 256-thread block
+    const uint32_t hm0 = best_hm;
+    for (uint32_t hm : {64u, 256u})
+      if ((rc = trial(best_g, best_block, hm, nullptr))) return rc;
+    if ((rc = trial(best_g, 256, best_hm, nullptr))) return rc;
+    (void)hm0;
     // keep the winner; the scratch shrinks to its group count
-    b->p = best_p;
+    for (auto& q : b->hq) q.heavy_min = best_hm;
+    b->p.heavy_min = best_hm;
+    if ((rc = batch_upload(b))) return rc;
     if (b->pool == &b->own && b->own.count > best_g) b->own.release();
     if ((rc = batch_configure(b, best_g, best_block))) return rc;
     if (b->exec) {
@@ -2339,6 +2407,7 @@ int eic_batch_info(const eic_batch* b, eic_batch_config* out) {
   out->block_threads = b->block;
   out->cuda_graph = b->exec ? 1u : 0u;
   out->gap_shift = b->p.gap_shift;
+  for (const auto& q : b->hq) out->gap_shift = q.gap_shift > out->gap_shift ? q.gap_shift : out->gap_shift;
   out->heavy_min = b->p.heavy_min;
   out->queries = b->nq;
   out->scratch_bytes = (uint64_t)b->pool->count * b->pool->slot_bytes;
@@ -2522,4 +2591,47 @@ int eic_serve_launch(const ServeArgs& args, uint32_t groups, uint32_t block, cud
   EIC_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)k_eic_serve, dim3(groups * args.nb), dim3(block), kargs, 0,
                                            stream));
   return EIC_OK;
+}
+
+int eic_tune_step_width(const eic_graph* g, uint32_t source, uint32_t copies, uint32_t nb, const eic_params& p,
+                        uint32_t from, cudaStream_t stream, uint32_t* best_shift, double* best_ms) {
+  if (!g || copies == 0 || source >= g->dg.n) return EIC_EINVAL;
+  *best_shift = from;
+  *best_ms = 0.0;
+  if (g->dg.two_m == 0) return EIC_OK;
+  uint32_t* buf = nullptr;
+  const uint64_t n = g->dg.n;
+  if (cudaMalloc((void**)&buf, n * 4 * copies) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return EIC_ENOMEM;
+  }
+  std::vector<const eic_graph*> gs(copies, g);
+  std::vector<uint32_t> ss(copies, source);
+  std::vector<uint32_t*> ds;
+  for (uint32_t k = 0; k < copies; ++k) ds.push_back(buf + n * k);
+  eic_batch* b = nullptr;
+  int rc = batch_create(gs.data(), ss.data(), copies, ds.data(), &p, nullptr, &b);
+  if (rc == EIC_OK) rc = batch_configure(b, copies, p.block_threads ? p.block_threads : kDefaultBlock, nb);
+  double t_best = -1.0;
+  for (uint32_t shift = from; rc == EIC_OK && shift <= 8; ++shift) {
+    for (auto& q : b->hq) q.gap_shift = shift;
+    if ((rc = batch_upload(b))) break;
+    double t = batch_time(b, stream);
+    const double t2 = batch_time(b, stream);
+    if (t < 0 || t2 < 0) {
+      rc = EIC_ECUDA;
+      break;
+    }
+    t = t2 < t ? t2 : t;
+    if (t_best < 0 || t < 0.98 * t_best) {
+      t_best = t;
+      *best_shift = shift;
+    } else {
+      break;
+    }
+  }
+  if (b) batch_free(b);
+  cudaFree(buf);
+  *best_ms = t_best;
+  return rc;
 }

@@ -72,6 +72,7 @@ def test_host_only_calls(lib):
     assert lib.eic_server_release(None, 0) == binding.EINVAL
     assert lib.eic_server_stats(None, None) == binding.EINVAL
     assert lib.eic_server_reset_stats(None) == binding.EINVAL
+    assert lib.eic_server_tune(None, None, None) == binding.EINVAL
     assert lib.eic_server_destroy(None) == binding.OK
 
 

@@ -157,3 +157,28 @@ def test_destroy_with_requests_pending(resident):
     t0 = time.time()
     srv.close()
     assert time.time() - t0 < 30
+
+
+def test_tuned_server_stays_exact(resident):
+    graphs, oracles = resident
+    want = _Want(graphs, oracles)
+    srv = eic.Server(graphs, groups=4)
+    shifts = srv.tune([0] * len(graphs))
+    assert len(shifts) == len(graphs) and all(0 <= x <= 8 for x in shifts)
+    rng = np.random.default_rng(8)
+    reqs = [(int(g), int(rng.integers(graphs[g].n))) for g in rng.integers(0, len(graphs), 40)]
+    tickets = [srv.submit(g, s) for g, s in reqs]
+    for t, (g, s) in zip(tickets, reqs):
+        assert srv.wait(t) == 0
+        got, _ = srv.result(t, graphs[g].n)
+        assert np.array_equal(got, want(g, s)), (g, s)
+        srv.release(t)
+    # tuning needs an idle server
+    t = srv.submit(0, 1)
+    try:
+        srv.tune([0] * len(graphs))
+    except eic.EicError as e:
+        assert e.status == binding.EBUSY
+    srv.wait(t)
+    srv.release(t)
+    srv.close()
