@@ -47,6 +47,7 @@ namespace {
 
 constexpr uint32_t kModePush = 0;     // frontier or push-set vertex: relax its window
 constexpr uint32_t kModePull = 2;     // unsettled vertex pulling over its light prefix
+constexpr uint32_t kKindNone = 0, kKindVertex = 1, kKindPush = 2, kKindPull = 3;  // a lane's item in a round
 constexpr uint32_t kNone = 0xFFFFFFFFu;
 constexpr int kShRanks = 1024;
 constexpr int kShRing = 2048;
@@ -98,6 +99,7 @@ constexpr uint32_t kTaskLen = 64;     // adjacency entries per grid task
 constexpr uint32_t kCursorMin = 16;   // rows longer than this keep a window cursor
 constexpr uint32_t kPullFast = 4;     // pull prefixes shorter than this are answered by their lane
 constexpr uint32_t kSweepNum = 1, kSweepDen = 2;  // sweep the pull set when it holds >= 1/2 of the vertices
+constexpr uint32_t kSweepChunk = 16;  // settled-bitmap words a warp takes at a time in a sweep (<= 32)
 constexpr uint32_t kStageT = 1024;    // tasks staged per block
 constexpr uint32_t kWarpStage = 256;  // next-frontier / settled-list appends staged per warp
 
@@ -212,6 +214,17 @@ __device__ __forceinline__ void tl_block(const KArgs& A, uint32_t kind, uint32_t
     A.timeline[2 * i] = t;
     A.timeline[2 * i + 1] = ((unsigned long long)kind << 32) | ((unsigned long long)qblock(A) << 48) | rid;
   }
+}
+
+// position of the k-th (from 0) set bit of m; m has more than k set bits
+__device__ __forceinline__ uint32_t kth_set_bit(uint32_t m, uint32_t k) {
+  uint32_t p = 0;
+#pragma unroll
+  for (uint32_t half = 16; half >= 1; half >>= 1) {
+    const uint32_t low = (uint32_t)__popc(m & ((1u << (p + half)) - 1u));  // set bits below p + half
+    if (low <= k) p += half;
+  }
+  return p;
 }
 
 __device__ __forceinline__ int64_t d64(uint32_t d) { return d == EIC_INF ? EIC_INF_T : (int64_t)d; }
@@ -391,7 +404,9 @@ __device__ void round_phase(const KArgs& A, const RoundCtx& R, const Local& L, R
                             uint32_t nitems, bool round1, const uint32_t* qin, Counters& C) {
   const uint32_t tid = threadIdx.x, nt = blockDim.x, lane = lane_id(), warp = tid >> 5;
   const uint32_t np = round1 ? L.push_end - L.push_beg : 0;
-  const uint32_t npp = np + L.pull_cnt;
+  const bool sweep = round1 && L.pull_sweep;  // the pull set is every unsettled vertex, swept below
+  const uint32_t npp = np + (sweep ? 0u : L.pull_cnt);
+  const uint32_t nlisted = sweep ? nitems - L.pull_cnt : nitems;  // items of the listed part
   const uint32_t gwarp = qblock(A) * (nt >> 5) + warp, nwarps = A.nb * (nt >> 5);
   const int64_t pull_bound = R.ub - R.st;
   WarpScr& W = S.w[warp];
@@ -401,7 +416,7 @@ __device__ void round_phase(const KArgs& A, const RoundCtx& R, const Local& L, R
   // end} (push set, from the settled list) or the pull-list entry. The next
   // iteration's record is loaded while this iteration runs.
   auto fetch = [&](uint32_t ii) -> uint4 {
-    if (ii >= nitems) return make_uint4(0u, 0u, 0u, 0u);
+    if (ii >= nlisted) return make_uint4(0u, 0u, 0u, 0u);
     if (!round1) return make_uint4(ld_list(&qin[ii]), 0u, 0u, 0u);
     if (ii >= npp) return make_uint4(L.s_int, 0u, 0u, 0u);
     if (ii < np) {
@@ -409,23 +424,16 @@ __device__ void round_phase(const KArgs& A, const RoundCtx& R, const Local& L, R
       const uint2 rr = ld_list2(&A.srow[idx]);
       return make_uint4(ld_list(&A.sd[idx]), rr.x, rr.y, 0u);
     }
-    if (L.pull_sweep) {  // every vertex in id order: {vertex, settled word, row begin, row end}
-      const uint32_t v = ii - np;
-      return make_uint4(v, __ldcg(&A.sbits[v >> 5]), __ldg(&A.G.row[v]), __ldg(&A.G.row[v + 1]));
-    }
     return ld_stream4(&A.G.nz[ii - np]);
   };
-  uint4 pre = fetch(gwarp * 32 + lane);
-  for (uint32_t base = gwarp * 32; base < nitems; base += nwarps * 32) {
-    const uint32_t i = base + lane;
-    const uint4 rec = pre;
-    pre = fetch(base + nwarps * 32 + lane);
+  // one warp iteration: each lane's item (kind kKindNone: no item)
+  auto step_items = [&](const uint4 rec, const uint32_t i, const uint32_t kind) {
     uint32_t u = 0, val = EIC_INF, b = 0, len = 0, mode = kModePush;
     uint32_t pfast = EIC_INF;       // best pull candidate of the lane's vertex
     bool plong = false;             // its prefix is longer than kPullFast entries
     uint32_t pbeg = 0, pend = 0;    // the rest of its row, scanned by the warp
-    if (i < nitems) {
-      if (!round1 || i >= npp) {  // frontier vertex (or the source, once)
+    if (kind != kKindNone) {
+      if (kind == kKindVertex) {  // frontier vertex (or the source, once)
         u = rec.x;
         const uint32_t d = __ldcg(&A.dist[u]);
         const uint32_t rb = __ldg(&A.G.row[u]), re = __ldg(&A.G.row[u + 1]);
@@ -440,7 +448,7 @@ __device__ void round_phase(const KArgs& A, const RoundCtx& R, const Local& L, R
             len = e - b;
           }
         }
-      } else if (i < np) {  // push set: settled, lb0 <= dist <= st (all from the settled list)
+      } else if (kind == kKindPush) {  // push set: settled, lb0 <= dist <= st (all from the settled list)
         const uint32_t idx = L.push_beg + i;
         const uint32_t d = rec.x;
         val = d;
@@ -465,19 +473,19 @@ __device__ void round_phase(const KArgs& A, const RoundCtx& R, const Local& L, R
         if (!((bits >> (u & 31)) & 1u)) {  // unsettled: its row's first kPullFast entries, together
           const uint32_t rl = z.w - z.z;
           uint2 ent[kPullFast];
-#pragma unroll
+  #pragma unroll
           for (uint32_t k = 0; k < kPullFast; ++k)
             ent[k] = k < rl ? ld_stream(&A.G.adj[z.z + k]) : make_uint2(0u, EIC_INF);
           uint32_t c = 0;  // the prefix with w < ub - st (rows are weight-sorted)
-#pragma unroll
+  #pragma unroll
           for (uint32_t k = 0; k < kPullFast; ++k) c += (k < rl && (int64_t)ent[k].y < pull_bound) ? 1u : 0u;
           C.pitems += c > 0 ? 1 : 0;  // in the pull set iff its lightest edge is below the bound
           plong = c == kPullFast && rl > kPullFast;  // the prefix goes on: the warp scans the rest
           {  // the loaded part of the prefix, answered in the lane
             uint32_t dv[kPullFast];
-#pragma unroll
+  #pragma unroll
             for (uint32_t k = 0; k < kPullFast; ++k) dv[k] = k < c ? __ldcg(&A.dist[ent[k].x]) : EIC_INF;
-#pragma unroll
+  #pragma unroll
             for (uint32_t k = 0; k < kPullFast; ++k) {
               if (k >= c) continue;
               C.trav += 1;
@@ -577,6 +585,71 @@ __device__ void round_phase(const KArgs& A, const RoundCtx& R, const Local& L, R
     }
     on_success(A, R, pok, u, pbest, pold, C, Qw, Fw);
     __syncwarp();
+  };
+  uint4 pre = fetch(gwarp * 32 + lane);
+  for (uint32_t base = gwarp * 32; base < nlisted; base += nwarps * 32) {
+    const uint32_t i = base + lane;
+    const uint4 rec = pre;
+    pre = fetch(base + nwarps * 32 + lane);
+    step_items(rec, i, i >= nlisted ? kKindNone : (!round1 || i >= npp) ? kKindVertex : i < np ? kKindPush : kKindPull);
+  }
+  if (sweep) {
+    // Function 1's pull set swept in vertex order, compacted: a warp takes
+    // kSweepChunk settled-bitmap words (32 vertices each) at a time and hands
+    // its lanes only the unsettled vertices, 32 per iteration, the next
+    // batch's row bounds loaded while the current one runs
+    const uint32_t ni = A.G.ni, nwords = (ni + 31) >> 5, nchunks = (nwords + kSweepChunk - 1) / kSweepChunk;
+    uint32_t ch = gwarp, m = 0, off = 0, tot = 0, r0 = 0, wn = ~0u;
+    auto word_at = [&](uint32_t c) -> uint32_t {
+      const uint32_t wi = c * kSweepChunk + lane;
+      return c < nchunks && lane < kSweepChunk && wi < nwords ? __ldcg(&A.sbits[wi]) : ~0u;
+    };
+    auto open_chunk = [&](uint32_t word) {  // this lane's unsettled mask, its exclusive rank, the chunk total
+      const uint32_t wi = ch * kSweepChunk + lane;
+      uint32_t mm = lane < kSweepChunk && wi < nwords ? ~word : 0u;
+      if (wi == nwords - 1 && (ni & 31u)) mm &= (1u << (ni & 31u)) - 1u;
+      m = mm;
+      const uint32_t c = __popc(mm), inc = warp_incl_scan(c);
+      off = inc - c;
+      tot = __shfl_sync(EIC_FULL_MASK, inc, 31);
+      r0 = 0;
+    };
+    if (ch < nchunks) {
+      open_chunk(word_at(ch));
+      wn = word_at(ch + nwarps);
+    }
+    auto next_batch = [&](bool& ok) -> uint4 {
+      while (r0 >= tot && ch < nchunks) {  // warp-uniform: skip to the next chunk with unsettled vertices
+        ch += nwarps;
+        if (ch >= nchunks) break;
+        open_chunk(wn);
+        wn = word_at(ch + nwarps);
+      }
+      ok = false;
+      if (ch >= nchunks) return make_uint4(0u, 0u, 0u, 0u);
+      const uint32_t r = r0 + lane;
+      r0 += 32;
+      uint32_t l = 0;  // the last word whose exclusive rank is <= r
+#pragma unroll
+      for (uint32_t h = 16; h > 0; h >>= 1) {
+        const uint32_t o = __shfl_sync(EIC_FULL_MASK, off, l + h);
+        if (o <= r) l += h;
+      }
+      const uint32_t ml = __shfl_sync(EIC_FULL_MASK, m, l), ol = __shfl_sync(EIC_FULL_MASK, off, l);
+      if (r >= tot) return make_uint4(0u, 0u, 0u, 0u);
+      ok = true;
+      const uint32_t v = ((ch * kSweepChunk + l) << 5) + kth_set_bit(ml, r - ol);
+      return make_uint4(v, 0u, __ldg(&A.G.row[v]), __ldg(&A.G.row[v + 1]));  // {vertex, settled word 0, row}
+    };
+    bool okc = false;
+    uint4 cur = next_batch(okc);
+    while (__any_sync(EIC_FULL_MASK, okc)) {
+      bool okn = false;
+      const uint4 nx = next_batch(okn);
+      step_items(cur, 0u, okc ? kKindPull : kKindNone);
+      cur = nx;
+      okc = okn;
+    }
   }
   warp_flush(Qw);
   warp_flush(Fw);
@@ -1271,10 +1344,24 @@ __global__ void k_init(KArgs A) {
 
 // Distances in the caller's numbering: out[u] = dist[orig2int[u]], +inf for
 // isolated vertices, 0 for the source.
+// Each thread has kOutIlp independent gathers in flight.
+constexpr uint32_t kOutIlp = 4;
 __global__ void k_output(DevGraph G, const uint32_t* __restrict__ idist, uint32_t s, uint32_t* out) {
-  for (uint64_t u = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; u < G.n; u += (uint64_t)gridDim.x * blockDim.x) {
-    const uint32_t i = __ldg(&G.orig2int[u]);
-    out[u] = u == s ? 0u : (i == EIC_INF ? EIC_INF : __ldcg(&idist[i]));
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t u0 = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; u0 < G.n; u0 += kOutIlp * stride) {
+    uint32_t i[kOutIlp], d[kOutIlp];
+#pragma unroll
+    for (uint32_t k = 0; k < kOutIlp; ++k) {
+      const uint64_t u = u0 + k * stride;
+      i[k] = u < G.n ? __ldg(&G.orig2int[u]) : EIC_INF;
+    }
+#pragma unroll
+    for (uint32_t k = 0; k < kOutIlp; ++k) d[k] = i[k] == EIC_INF ? EIC_INF : __ldcg(&idist[i[k]]);
+#pragma unroll
+    for (uint32_t k = 0; k < kOutIlp; ++k) {
+      const uint64_t u = u0 + k * stride;
+      if (u < G.n) out[u] = u == s ? 0u : d[k];
+    }
   }
 }
 
@@ -1761,7 +1848,7 @@ int enqueue_query(eic_graph* g, uint32_t s, uint32_t* dist, uint32_t* parent, co
   if (ev0) EIC_CUDA_TRY(cudaEventRecord(ev0, st));
   EIC_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)k_eic, dim3(w.grid), dim3(block), args, 0, st));
   if (ev1) EIC_CUDA_TRY(cudaEventRecord(ev1, st));
-  k_output<<<2 * w.grid, 256, 0, st>>>(g->dg, w.idist, s, dist);
+  k_output<<<4 * w.grid, 256, 0, st>>>(g->dg, w.idist, s, dist);
   EIC_CUDA_TRY(cudaGetLastError());
   if (parent) {
     k_parent<<<1024, 256, 0, st>>>(g->dg, w.idist, s, parent);
@@ -2561,7 +2648,7 @@ extern "C" int eic_sssp_noalloc(const eic_graph* gc, uint32_t source, uint32_t* 
   EIC_CUDA_TRY(cudaGetLastError());
   void* args[] = {&A};
   EIC_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)k_eic, dim3(nd.grid), dim3(kDefaultBlock), args, 0, st));
-  k_output<<<2 * nd.grid, 256, 0, st>>>(G, A.dist, source, dist);
+  k_output<<<4 * nd.grid, 256, 0, st>>>(G, A.dist, source, dist);
   EIC_CUDA_TRY(cudaGetLastError());
   int status = 0;
   EIC_CUDA_TRY(cudaMemcpyAsync(&status, &ctl->status, sizeof(int), cudaMemcpyDeviceToHost, st));
