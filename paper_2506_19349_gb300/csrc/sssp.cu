@@ -51,6 +51,7 @@ constexpr uint32_t kKindNone = 0, kKindVertex = 1, kKindPush = 2, kKindPull = 3;
 constexpr uint32_t kNone = 0xFFFFFFFFu;
 constexpr int kShRanks = 1024;
 constexpr int kShRing = 2048;
+constexpr int64_t kRingNarrow = 16;  // statistics windows up to this width aggregate ring updates per warp
 
 struct KArgs {
   DevGraph G;
@@ -1152,6 +1153,7 @@ __device__ void run_query(const KArgs& A, QueryShared& Q, uint32_t& gen) {
       const bool has = lbeg + qb * blockDim.x < lend;  // this block has settled vertices to count
       const int64_t wlo = L.ub - (int64_t)A.G.maxw > L.lb ? L.ub - (int64_t)A.G.maxw : L.lb;
       const bool ring_sh = A.ring_shift == 0 && L.ub < EIC_INF_T && (L.ub - wlo) <= kShRing;
+      const bool ring_narrow = ring_sh && (L.ub - wlo) <= kRingNarrow && A.G.max_deg < (1u << 27);  // (in shared memory)
       if (has) {
         for (int r = threadIdx.x; r < kShRanks; r += blockDim.x) S.hist[r] = 0;
         if (ring_sh)
@@ -1193,22 +1195,31 @@ __device__ void run_query(const KArgs& A, QueryShared& Q, uint32_t& gen) {
             __stcg(&A.scur[idx], dg > kCursorMin ? __ldcg(&A.cursor[x]) : kNone);
             __stcg(&A.srow[idx], make_uint2(xrb, xre));
           }
-          if (dg > 0) {  // degree-0 vertices (an isolated source) carry no rank
-            const uint32_t r = __ldg(&A.G.drank[dg]);
-            if (r < (uint32_t)kShRanks)
-              atomicAdd(&S.hist[r], 1u);
-            else
-              atomicSub(&A.hist[r], 1u);
-          }
           bdeg += dg;
           bmax = d > bmax ? d : bmax;
           bany = 1;
-          if ((int64_t)d >= wlo) {
-            if (ring_sh)
-              atomicAdd(&S.ring[d - wlo], (unsigned long long)dg);
-            else
-              atomicAdd(&A.ring[((uint64_t)d >> A.ring_shift) & A.ring_mask], (unsigned long long)dg);
-          }
+        }
+        // degree histogram (degree-0 vertices, an isolated source, carry no rank)
+        const uint32_t r = take && xre > xrb ? __ldg(&A.G.drank[xre - xrb]) : EIC_INF;
+        if (r < (uint32_t)kShRanks)
+          atomicAdd(&S.hist[r], 1u);
+        else if (r != EIC_INF)
+          atomicSub(&A.hist[r], 1u);
+        // D(x) ring: in a narrow window the step's settled vertices share few
+        // distances; then one atomic per distinct slot in the warp, with the
+        // group's degree sum (32-bit while 32 degrees cannot overflow it)
+        const bool rk = take && (int64_t)d >= wlo;
+        const uint32_t slot = rk ? (ring_sh ? (uint32_t)(d - wlo) : (uint32_t)(((uint64_t)d >> A.ring_shift) & A.ring_mask))
+                                 : EIC_INF;
+        if (ring_narrow) {
+          const uint32_t rg = __match_any_sync(EIC_FULL_MASK, slot);
+          const uint32_t sum = __reduce_add_sync(rg, rk ? xre - xrb : 0u);
+          if (rk && lane_id() == (uint32_t)__ffs(rg) - 1) atomicAdd(&S.ring[slot], (unsigned long long)sum);
+        } else if (rk) {
+          if (ring_sh)
+            atomicAdd(&S.ring[slot], (unsigned long long)(xre - xrb));
+          else
+            atomicAdd(&A.ring[slot], (unsigned long long)(xre - xrb));
         }
       }
       __syncthreads();
