@@ -416,10 +416,15 @@ __device__ void round_phase(const KArgs& A, const RoundCtx& R, const Local& L, R
   // an item's record: the vertex (frontier, source), {dist, row begin, row
   // end} (push set, from the settled list) or the pull-list entry. The next
   // iteration's record is loaded while this iteration runs.
-  auto fetch = [&](uint32_t ii) -> uint4 {
+  // A frontier vertex's record {vertex, dist, row begin, row end} is loaded
+  // one iteration ahead, its queue entry two iterations ahead.
+  auto fetch_id = [&](uint32_t ii) -> uint32_t { return !round1 && ii < nlisted ? ld_list(&qin[ii]) : 0u; };
+  auto fetch = [&](uint32_t ii, uint32_t id) -> uint4 {
     if (ii >= nlisted) return make_uint4(0u, 0u, 0u, 0u);
-    if (!round1) return make_uint4(ld_list(&qin[ii]), 0u, 0u, 0u);
-    if (ii >= npp) return make_uint4(L.s_int, 0u, 0u, 0u);
+    if (!round1 || ii >= npp) {  // frontier vertex (or the source, once)
+      const uint32_t u = round1 ? L.s_int : id;
+      return make_uint4(u, __ldcg(&A.dist[u]), __ldg(&A.G.row[u]), __ldg(&A.G.row[u + 1]));
+    }
     if (ii < np) {
       const uint32_t idx = L.push_beg + ii;
       const uint2 rr = ld_list2(&A.srow[idx]);
@@ -436,8 +441,7 @@ __device__ void round_phase(const KArgs& A, const RoundCtx& R, const Local& L, R
     if (kind != kKindNone) {
       if (kind == kKindVertex) {  // frontier vertex (or the source, once)
         u = rec.x;
-        const uint32_t d = __ldcg(&A.dist[u]);
-        const uint32_t rb = __ldg(&A.G.row[u]), re = __ldg(&A.G.row[u + 1]);
+        const uint32_t d = rec.y, rb = rec.z, re = rec.w;
         val = d;
         if (d != EIC_INF && !(d > 0 && re - rb == 1)) {  // Paths excludes leaves (Algorithm 1)
           C.frontier += 1;
@@ -542,39 +546,60 @@ __device__ void round_phase(const KArgs& A, const RoundCtx& R, const Local& L, R
     W.u[lane] = u;
     W.mode[lane] = mode;
     __syncwarp();
-    for (uint32_t g0 = 0; g0 < total; g0 += 32) {
-      const uint32_t g = g0 + lane;
-      bool ok = false;
-      uint32_t v = 0, nd = 0, old = 0;
-      if (g < total) {
-        uint32_t lo = 0, hi = 31;
-        while (lo < hi) {  // last lane whose window starts at or before g
-          const uint32_t mid = (lo + hi + 1) >> 1;
-          if (W.excl[mid] <= g)
-            lo = mid;
-          else
-            hi = mid - 1;
-        }
-        const uint2 ent = ld_stream(&A.G.adj[W.beg[lo] + (g - W.excl[lo])]);
-        v = ent.x;
-        if (W.mode[lo] != kModePull) {
-          C.trav += 1;
-          nd = W.val[lo] + ent.y;  // inside [lb, min(ub, 2^32-1)) by the window bounds
-          const uint32_t dv = __ldcg(&A.dist[v]);
-          if (nd < dv) {
-            old = atomicMin(&A.dist[v], nd);
-            ok = nd < old;
+    // the concatenated windows, two entries per lane at a time (both entries'
+    // loads in flight together)
+    for (uint32_t g0 = 0; g0 < total; g0 += 64) {
+      uint32_t own[2], dv[2], nd[2], old[2];
+      uint2 ent[2];
+      bool act[2], push[2], ok[2];
+#pragma unroll
+      for (uint32_t h = 0; h < 2; ++h) {
+        const uint32_t g = g0 + h * 32 + lane;
+        act[h] = g < total;
+        own[h] = 0;
+        ent[h] = make_uint2(0u, 0u);
+        if (act[h]) {
+          uint32_t lo = 0, hi = 31;
+          while (lo < hi) {  // last lane whose window starts at or before g
+            const uint32_t mid = (lo + hi + 1) >> 1;
+            if (W.excl[mid] <= g)
+              lo = mid;
+            else
+              hi = mid - 1;
           }
-        } else if ((int64_t)ent.y < pull_bound) {  // request answered by a settled v with st <= dist[v] < lb
-          C.trav += 1;
-          C.pulls += 1;
-          const uint32_t dv = __ldcg(&A.dist[v]);
-          const int64_t dvv = dv;
-          if (dv != EIC_INF && dvv >= R.st && dvv < R.lb && dvv + ent.y < R.ub)
-            atomicMin(&W.val[lo], (uint32_t)(dvv + ent.y));
+          own[h] = lo;
+          ent[h] = ld_stream(&A.G.adj[W.beg[lo] + (g - W.excl[lo])]);
         }
       }
-      on_success(A, R, ok, v, nd, old, C, Qw, Fw);
+#pragma unroll
+      for (uint32_t h = 0; h < 2; ++h) {
+        push[h] = act[h] && W.mode[own[h]] != kModePull;
+        // a pull entry is a request answered by a settled v with st <= dist[v] < lb
+        act[h] = push[h] || (act[h] && (int64_t)ent[h].y < pull_bound);
+        dv[h] = act[h] ? __ldcg(&A.dist[ent[h].x]) : EIC_INF;
+      }
+#pragma unroll
+      for (uint32_t h = 0; h < 2; ++h) {
+        ok[h] = false;
+        nd[h] = 0;
+        old[h] = 0;
+        if (push[h]) {
+          C.trav += 1;
+          nd[h] = W.val[own[h]] + ent[h].y;  // inside [lb, min(ub, 2^32-1)) by the window bounds
+          if (nd[h] < dv[h]) {
+            old[h] = atomicMin(&A.dist[ent[h].x], nd[h]);
+            ok[h] = nd[h] < old[h];
+          }
+        } else if (act[h]) {
+          C.trav += 1;
+          C.pulls += 1;
+          const int64_t dvv = dv[h];
+          if (dv[h] != EIC_INF && dvv >= R.st && dvv < R.lb && dvv + ent[h].y < R.ub)
+            atomicMin(&W.val[own[h]], (uint32_t)(dvv + ent[h].y));
+        }
+      }
+      on_success(A, R, ok[0], ent[0].x, nd[0], old[0], C, Qw, Fw);
+      on_success(A, R, ok[1], ent[1].x, nd[1], old[1], C, Qw, Fw);
     }
     __syncwarp();
     bool pok = false;
@@ -587,11 +612,14 @@ __device__ void round_phase(const KArgs& A, const RoundCtx& R, const Local& L, R
     on_success(A, R, pok, u, pbest, pold, C, Qw, Fw);
     __syncwarp();
   };
-  uint4 pre = fetch(gwarp * 32 + lane);
-  for (uint32_t base = gwarp * 32; base < nlisted; base += nwarps * 32) {
+  const uint32_t stride = nwarps * 32;
+  uint4 pre = fetch(gwarp * 32 + lane, fetch_id(gwarp * 32 + lane));
+  uint32_t idn = fetch_id(gwarp * 32 + stride + lane);
+  for (uint32_t base = gwarp * 32; base < nlisted; base += stride) {
     const uint32_t i = base + lane;
     const uint4 rec = pre;
-    pre = fetch(base + nwarps * 32 + lane);
+    pre = fetch(base + stride + lane, idn);
+    idn = fetch_id(base + 2 * stride + lane);
     step_items(rec, i, i >= nlisted ? kKindNone : (!round1 || i >= npp) ? kKindVertex : i < np ? kKindPush : kKindPull);
   }
   if (sweep) {
