@@ -98,8 +98,9 @@ constexpr uint32_t kMaxBlock = 512;
 constexpr uint32_t kMaxWarps = kMaxBlock / 32;
 constexpr uint32_t kTaskLen = 64;     // adjacency entries per grid task
 constexpr uint32_t kCursorMin = 16;   // rows longer than this keep a window cursor
-constexpr uint32_t kPullFast = 4;     // pull prefixes shorter than this are answered by their lane
+constexpr uint32_t kPullFast = 8;     // pull prefixes up to this long are answered by their lane
 constexpr uint32_t kSweepNum = 1, kSweepDen = 2;  // sweep the pull set when it holds >= 1/2 of the vertices
+constexpr uint32_t kRelaxIlp = 2;     // window entries a lane relaxes at a time
 constexpr uint32_t kSweepChunk = 16;  // settled-bitmap words a warp takes at a time in a sweep (<= 32)
 constexpr uint32_t kStageT = 1024;    // tasks staged per block
 constexpr uint32_t kWarpStage = 256;  // next-frontier / settled-list appends staged per warp
@@ -546,14 +547,14 @@ __device__ void round_phase(const KArgs& A, const RoundCtx& R, const Local& L, R
     W.u[lane] = u;
     W.mode[lane] = mode;
     __syncwarp();
-    // the concatenated windows, two entries per lane at a time (both entries'
+    // the concatenated windows, kRelaxIlp entries per lane at a time (their
     // loads in flight together)
-    for (uint32_t g0 = 0; g0 < total; g0 += 64) {
-      uint32_t own[2], dv[2], nd[2], old[2];
-      uint2 ent[2];
-      bool act[2], push[2], ok[2];
+    for (uint32_t g0 = 0; g0 < total; g0 += 32 * kRelaxIlp) {
+      uint32_t own[kRelaxIlp], dv[kRelaxIlp], nd[kRelaxIlp], old[kRelaxIlp];
+      uint2 ent[kRelaxIlp];
+      bool act[kRelaxIlp], push[kRelaxIlp], ok[kRelaxIlp];
 #pragma unroll
-      for (uint32_t h = 0; h < 2; ++h) {
+      for (uint32_t h = 0; h < kRelaxIlp; ++h) {
         const uint32_t g = g0 + h * 32 + lane;
         act[h] = g < total;
         own[h] = 0;
@@ -572,14 +573,14 @@ __device__ void round_phase(const KArgs& A, const RoundCtx& R, const Local& L, R
         }
       }
 #pragma unroll
-      for (uint32_t h = 0; h < 2; ++h) {
+      for (uint32_t h = 0; h < kRelaxIlp; ++h) {
         push[h] = act[h] && W.mode[own[h]] != kModePull;
         // a pull entry is a request answered by a settled v with st <= dist[v] < lb
         act[h] = push[h] || (act[h] && (int64_t)ent[h].y < pull_bound);
         dv[h] = act[h] ? __ldcg(&A.dist[ent[h].x]) : EIC_INF;
       }
 #pragma unroll
-      for (uint32_t h = 0; h < 2; ++h) {
+      for (uint32_t h = 0; h < kRelaxIlp; ++h) {
         ok[h] = false;
         nd[h] = 0;
         old[h] = 0;
@@ -598,8 +599,8 @@ __device__ void round_phase(const KArgs& A, const RoundCtx& R, const Local& L, R
             atomicMin(&W.val[own[h]], (uint32_t)(dvv + ent[h].y));
         }
       }
-      on_success(A, R, ok[0], ent[0].x, nd[0], old[0], C, Qw, Fw);
-      on_success(A, R, ok[1], ent[1].x, nd[1], old[1], C, Qw, Fw);
+#pragma unroll
+      for (uint32_t h = 0; h < kRelaxIlp; ++h) on_success(A, R, ok[h], ent[h].x, nd[h], old[h], C, Qw, Fw);
     }
     __syncwarp();
     bool pok = false;
