@@ -98,9 +98,12 @@ constexpr uint32_t kMaxBlock = 512;
 constexpr uint32_t kMaxWarps = kMaxBlock / 32;
 constexpr uint32_t kTaskLen = 64;     // adjacency entries per grid task
 constexpr uint32_t kCursorMin = 16;   // rows longer than this keep a window cursor
-constexpr uint32_t kPullFast = 8;     // pull prefixes up to this long are answered by their lane
+// Round-phase shapes (pull prefix entries a lane answers itself, window
+// entries a lane relaxes at a time), per kernel: more of each is faster while
+// registers last; the batch and serving kernels hold more state.
+constexpr uint32_t kPullFastSingle = 8, kRelaxIlpSingle = 2;  // k_eic
+constexpr uint32_t kPullFastGroup = 4, kRelaxIlpGroup = 1;    // k_eic_batch, k_eic_serve
 constexpr uint32_t kSweepNum = 1, kSweepDen = 2;  // sweep the pull set when it holds >= 1/2 of the vertices
-constexpr uint32_t kRelaxIlp = 2;     // window entries a lane relaxes at a time
 constexpr uint32_t kSweepChunk = 16;  // settled-bitmap words a warp takes at a time in a sweep (<= 32)
 constexpr uint32_t kStageT = 1024;    // tasks staged per block
 constexpr uint32_t kWarpStage = 256;  // next-frontier / settled-list appends staged per warp
@@ -402,6 +405,7 @@ __device__ __forceinline__ void on_success(const KArgs& A, const RoundCtx& R, bo
 // relaxed by the warp over their concatenation, longer ones become grid tasks.
 // A pull reads the prefix of its vertex's row with weight < ub - st.
 // List appends are staged in shared memory and flushed once per block.
+template <uint32_t kPullFast, uint32_t kRelaxIlp>
 __device__ void round_phase(const KArgs& A, const RoundCtx& R, const Local& L, RoundScr& S, Stage& T,
                             uint32_t nitems, bool round1, const uint32_t* qin, Counters& C) {
   const uint32_t tid = threadIdx.x, nt = blockDim.x, lane = lane_id(), warp = tid >> 5;
@@ -1060,6 +1064,7 @@ struct QueryShared {
 // The query loop of Algorithm 1 run by the A.nb blocks of one query: rounds
 // of a step (item phase, task phase), statistics pass, step boundary, until
 // termination. gen is the block's copy of the barrier generation.
+template <uint32_t kPullFast, uint32_t kRelaxIlp>
 __device__ void run_query(const KArgs& A, QueryShared& Q, uint32_t& gen) {
   PhaseScr& P = Q.P;
   Stage& T = Q.T;
@@ -1131,7 +1136,7 @@ __device__ void run_query(const KArgs& A, QueryShared& Q, uint32_t& gen) {
       if (!L.pull_on) LL.pull_cnt = 0;
       const uint32_t nitems = round1 ? (LL.push_end - LL.push_beg) + LL.pull_cnt + LL.extra_s : L.cur_cnt;
       if (qb == 0 && threadIdx.x == 0) tl_mark(A, 8, nitems);  // diagnostic: the round's items
-      round_phase(A, R, LL, P.r, T, nitems, round1, qin, C);
+      round_phase<kPullFast, kRelaxIlp>(A, R, LL, P.r, T, nitems, round1, qin, C);
       if (!grid_barrier(&c->bar, &gen, A.nb, A.max_spin, &c->status)) {
         alive = false;
         break;
@@ -1320,7 +1325,7 @@ __device__ void run_query(const KArgs& A, QueryShared& Q, uint32_t& gen) {
 __global__ void __launch_bounds__(kMaxBlock, 2) k_eic(KArgs A) {
   __shared__ QueryShared Q;
   uint32_t gen = __ldcg(&A.ctl->bar.gen);
-  run_query(A, Q, gen);
+  run_query<kPullFastSingle, kRelaxIlpSingle>(A, Q, gen);
 }
 
 // Control block of a new query (one thread): the source's distance, the
@@ -1534,7 +1539,7 @@ __global__ void __launch_bounds__(kMaxBlock, 2) k_eic_batch(BatchArgs P) {
     }
     __syncthreads();
     if (!query_setup(sA, gen)) break;
-    run_query(sA, Q, gen);
+    run_query<kPullFastGroup, kRelaxIlpGroup>(sA, Q, gen);
     __syncthreads();
     if (ld_volatile_int(&c->status) != 0) break;
     query_output(sA);
@@ -1712,7 +1717,7 @@ __global__ void __launch_bounds__(kMaxBlock, 2) k_eic_serve(ServeArgs P) {
     }
     __syncthreads();
     if (!query_setup(sA, gen)) break;
-    run_query(sA, Q, gen);
+    run_query<kPullFastGroup, kRelaxIlpGroup>(sA, Q, gen);
     __syncthreads();
     if (ld_volatile_int(&c->status) != 0) break;
     query_output(sA);
