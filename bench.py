@@ -564,6 +564,8 @@ def main():
         src_host = torch.tensor(srcs, dtype=torch.int32).pin_memory()
         src_dev = torch.empty(q, dtype=torch.int32, device="cuda")
         host_out = [torch.empty(n, dtype=torch.int32).pin_memory() for _ in range(2)]
+        copy_stream = torch.cuda.Stream()  # each query's download overlaps the next query
+        copied = [None] * q
         torch.cuda.synchronize()
         if world > 1:
             torch.distributed.barrier()
@@ -574,8 +576,17 @@ def main():
             src_dev.copy_(src_host, non_blocking=True)
             srcs_now = src_dev.cpu().tolist()  # the query API takes host source ids
             for i, s in enumerate(srcs_now):
+                if copied[i] is not None:  # dists[i] is rewritten only after its last download
+                    stream.wait_event(copied[i])
                 eic.sssp(g, s, dist=dists[i])
-                host_out[i & 1].copy_(dists[i], non_blocking=True)
+                done = torch.cuda.Event()
+                done.record(stream)
+                copy_stream.wait_event(done)
+                with torch.cuda.stream(copy_stream):
+                    host_out[i & 1].copy_(dists[i], non_blocking=True)
+                    copied[i] = torch.cuda.Event()
+                    copied[i].record(copy_stream)
+        stream.wait_stream(copy_stream)  # the timed region ends after the last download
         e_end.record(stream)
         torch.cuda.synchronize()
         e2e_ms = max_over_ranks(e_start.elapsed_time(e_end), world, "cuda")
