@@ -54,6 +54,8 @@ def parse_args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched measurements")
     ap.add_argument("--no-served", action="store_true", help="skip the serving measurement")
+    ap.add_argument("--no-stress", action="store_true", help="skip the road-like and log-normal-weight workloads")
+    ap.add_argument("--stress-sources", type=int, default=16, help="sources per stress workload")
     return ap.parse_args()
 
 
@@ -354,6 +356,57 @@ def batched_mixed(eic, torch, stream, runs):
             "speedup": gteps / plain_gteps}
 
 
+def stress(eic, torch, stream, nsources):
+    """The stress workloads, on the plain path: the 4096^2 road-like grid
+    (weights [1,4095]) with the default step width and with the exact 16x
+    scaling the autotuners pick for grids, and Kron 25 with log-normal
+    weights. GTEPS = edges in the source's component / query time."""
+    import numpy as np
+    from paper_2506_19349_gb300 import graphgen
+
+    cases = (
+        ("road_4096", "4096^2 grid, 4-neighbour, 10% of edges deleted, 2% diagonal shortcuts, weights uniform "
+         "[1,4095], sources from the largest component",
+         lambda: graphgen.road(4096, seed=3, wmax=4095, nsources=nsources), (0, 4)),
+        ("kron25_lognormal", "kron25 topology, weights clamp(llround(exp(3 + 1.5 Z)), 1, 65535), sources uniform "
+         "over non-isolated vertices", lambda: graphgen.kron(25, seed=2, weights="lognormal", nsources=nsources),
+         (0,)),
+    )
+    out = {}
+    for name, desc, make, shifts in cases:
+        t0 = time.perf_counter()
+        wl = make()
+        gen_s = time.perf_counter() - t0
+        g = eic.Graph(wl.n, wl.src, wl.dst, wl.w)
+        srcs = [int(s) for s in wl.sources]
+        del wl
+        deg = _degrees(eic, g, torch)
+        d = eic.new_dist(g.n)
+        res = {"workload": desc, "n": g.n, "m": g.m, "sources": len(srcs), "generate_s": gen_s}
+        for sh in shifts:
+            p = eic.default_params(gap_shift=sh)
+            eic.sssp(g, srcs[0], dist=d, params=p)  # warm-up
+            ms, mc, steps, rounds = [], [], [], []
+            for s in srcs:
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                _, _, info = eic.sssp(g, s, dist=d, params=p, stats=True)
+                e1.record(stream)
+                e1.synchronize()
+                ms.append(e0.elapsed_time(e1))
+                mc.append(_m_c(deg, d))
+                steps.append(info["steps"])
+                rounds.append(info["rounds"])
+            res[f"gap_shift_{sh}"] = {"value": sum(mc) / (sum(ms) * 1e-3) / 1e9, "unit": "GTEPS",
+                                      "p50_ms": float(np.percentile(ms, 50)), "p99_ms": float(np.percentile(ms, 99)),
+                                      "steps_mean": statistics.mean(steps), "rounds_mean": statistics.mean(rounds)}
+        out[name] = res
+        del g, d, deg
+        torch.cuda.empty_cache()
+    return out
+
+
 def serving(eic, torch, stream, rates, seconds_per_rate, max_per_rate):
     """Resident set of 8 graphs (RMAT scales 18..23, a second scale-22 seed, a
     2048^2 grid), Poisson request streams at each rate through eic_server_*;
@@ -604,6 +657,10 @@ def main():
     if not args.no_served and world == 1:
         torch.cuda.empty_cache()
         served = serving(eic, torch, stream, (100, 1000, 5000, 20000, float("inf")), 1.0, 2000)
+    stressed = None
+    if not args.no_stress and world == 1:
+        torch.cuda.empty_cache()
+        stressed = stress(eic, torch, stream, args.stress_sources)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -636,6 +693,7 @@ def main():
                                         "pull_items")},
             "batched": batched,
             "served": served,
+            "stress": stressed,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
