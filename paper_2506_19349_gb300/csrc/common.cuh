@@ -83,6 +83,17 @@ __device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t* p) {
 
 __device__ __forceinline__ int ld_volatile_int(const int* p) { return *(const volatile int*)p; }
 
+// Release/acquire primitives of the barrier (gpu scope).
+__device__ __forceinline__ uint32_t atom_add_acq_rel_u32(uint32_t* p, uint32_t v) {
+  uint32_t old;
+  asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+  return old;
+}
+
+__device__ __forceinline__ void st_release_u32(uint32_t* p, uint32_t v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
 // ---------------------------------------------------- bounded grid barrier
 
 struct GridBarrier {
@@ -100,13 +111,14 @@ __device__ __forceinline__ bool grid_barrier(GridBarrier* bar, uint32_t* gen_loc
   __shared__ int s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
-    uint32_t g = *gen_local;
-    __threadfence();
-    uint32_t arrived = atomicAdd(&bar->count, 1u);
+    const uint32_t g = *gen_local;
+    // the arrival releases the block's writes (ordered before it by the block
+    // barrier) and, for the last block, acquires everyone else's; the new
+    // generation is published with a release after the count is reset
+    const uint32_t arrived = atom_add_acq_rel_u32(&bar->count, 1u);
     if (arrived == nblocks - 1) {
       bar->count = 0;
-      __threadfence();
-      atomicExch(&bar->gen, g + 1);
+      st_release_u32(&bar->gen, g + 1);
     } else {
       uint64_t spins = 0;
       while (ld_acquire_u32(&bar->gen) == g) {
@@ -119,7 +131,6 @@ __device__ __forceinline__ bool grid_barrier(GridBarrier* bar, uint32_t* gen_loc
       }
     }
     *gen_local = g + 1;
-    __threadfence();
     s_ok = ld_volatile_int(status) == 0;
   }
   __syncthreads();

@@ -897,8 +897,7 @@ __device__ void step_boundary(const KArgs& A, PhaseScr& P, BState& B, const Loca
   if (sh_flag[0]) {
     if (threadIdx.x == 0) {
       c->done = 1;
-      c->s2_done = 0;
-      __threadfence();
+      c->s2_done = 0;  // published by the grid barrier's release
     }
     __syncthreads();
     return;
@@ -999,8 +998,7 @@ __device__ void step_boundary(const KArgs& A, PhaseScr& P, BState& B, const Loca
     c->acc_deg = 0;
     c->acc_maxd1 = 0;
     c->s2_done = 0;
-    c->done = 0;
-    __threadfence();
+    c->done = 0;  // the control values are published by the grid barrier's release
   }
   __syncthreads();
 }
@@ -1280,8 +1278,7 @@ __device__ void run_query(const KArgs& A, QueryShared& Q, uint32_t& gen) {
         }
         if (v[0]) atomicAdd(&c->acc_deg, v[0]);
         if (v[1]) atomicMax(&c->acc_maxd1, (uint32_t)v[1]);
-        __threadfence();
-        atomicAdd(&c->s2_done, 1u);
+        atom_add_acq_rel_u32(&c->s2_done, 1u);  // releases the block's statistics
       }
       if (qb == 0) {  // block 0 waits (bounded) for every block's statistics
         if (threadIdx.x == 0) {
@@ -1294,7 +1291,6 @@ __device__ void run_query(const KArgs& A, QueryShared& Q, uint32_t& gen) {
               break;
             }
           }
-          __threadfence();
           tl_mark(A, 4, L.rid);
         }
         __syncthreads();
