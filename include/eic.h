@@ -84,7 +84,12 @@ typedef struct {
   uint64_t highd_lb;   /* highD(lb) */
   uint64_t rounds;     /* relaxation rounds (synchronisations) in the step */
   uint64_t settled;    /* vertices whose distance fell in [lb, ub) */
+  uint32_t flags;      /* EIC_STEP_* : how the step's first round was formed */
+  uint32_t reserved;
 } eic_step;
+
+#define EIC_STEP_PULL 1u  /* Function 1's pull ran (st < lb) */
+#define EIC_STEP_SWEPT 2u /* ... over the unsettled vertices in vertex order (its set held >= half of them) */
 
 /* Counters of one query (Section 4: nSync, nFrontier, nTrav before
  * normalisation). trace/trace_cap are inputs: when trace is a host array of

@@ -48,7 +48,11 @@ class BatchConfig(ctypes.Structure):
 class Step(ctypes.Structure):
     _fields_ = [("lb", ctypes.c_int64), ("ub", ctypes.c_int64), ("st", ctypes.c_int64), ("gap_lb", ctypes.c_int64),
                 ("sumd_lb", ctypes.c_uint64), ("highd_lb", ctypes.c_uint64), ("rounds", ctypes.c_uint64),
-                ("settled", ctypes.c_uint64)]
+                ("settled", ctypes.c_uint64), ("flags", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+
+
+STEP_PULL = 1   # EIC_STEP_PULL: Function 1's pull ran in the step (st < lb)
+STEP_SWEPT = 2  # EIC_STEP_SWEPT: the pull went over the unsettled vertices in vertex order
 
 
 class Stats(ctypes.Structure):

@@ -864,6 +864,8 @@ __device__ void step_boundary(const KArgs& A, PhaseScr& P, BState& B, const Loca
       r.highd_lb = B.highd_lb;
       r.rounds = rounds_in_step;
       r.settled = settled_now - L.step_off_cur;
+      r.flags = (L.pull_on ? EIC_STEP_PULL : 0u) | (L.pull_on && L.pull_sweep ? EIC_STEP_SWEPT : 0u);
+      r.reserved = 0;
       A.trace[k - 1] = r;
     }
     c->trace_len = k;

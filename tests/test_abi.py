@@ -98,7 +98,8 @@ def test_ctypes_mirrors_match_the_c_layout(tmp_path):
     if cc is None:
         pytest.skip("no C compiler")
     checks = {"eic_params": (binding.Params, ["beta", "st_num", "flags", "batch_groups", "reserved"]),
-              "eic_step": (binding.Step, ["lb", "ub", "st", "gap_lb", "sumd_lb", "highd_lb", "rounds", "settled"]),
+              "eic_step": (binding.Step, ["lb", "ub", "st", "gap_lb", "sumd_lb", "highd_lb", "rounds", "settled",
+                                          "flags", "reserved"]),
               "eic_stats": (binding.Stats, ["steps", "pull_items", "trace", "trace_cap", "trace_len", "timeline",
                                             "timeline_cap", "timeline_len", "kernel_ms"]),
               "eic_batch_config": (binding.BatchConfig, ["groups", "queries", "scratch_bytes", "tuned_ms"]),

@@ -91,6 +91,29 @@ def test_distances_bit_exact_and_trace(name, wl):
         ot = [{k: r[k] for k in keys} for r in otrace]
         assert gt == ot, f"{name} s={s}: trace differs at step {next(i for i, (a, b) in enumerate(zip(gt, ot)) if a != b) if len(gt) == len(ot) else 'len'}"
         assert info["steps"] == otot["steps"]
+        # the pull ran exactly in the steps with st < lb (Function 1), and only a pull is swept
+        for r in info["trace"]:
+            assert bool(r["flags"] & eic.STEP_PULL) == (r["st"] < r["lb"]), (name, s, r)
+            assert not (r["flags"] & eic.STEP_SWEPT) or r["flags"] & eic.STEP_PULL, (name, s, r)
+
+
+def test_sweep_and_listed_pulls_both_exercised():
+    """On Kronecker graphs both pull forms run and stay exact: the compacted
+    vertex-order sweep (every pull step of the smaller graphs) and the listed
+    pull over a prefix of the weight-ordered vertices (a step of one Kron 18
+    source, whose pull set holds fewer than half of the vertices)."""
+    kinds = set()
+    for scale, seed, weights in ((14, 21, "uniform255"), (13, 22, "lognormal"), (18, 2, "uniform255")):
+        wl = G.kron(scale, seed=seed, weights=weights, nsources=3)
+        g, og = _pair(wl)
+        for s in wl.sources:
+            dist, rc, info = eic.sssp(g, int(s), trace_cap=4096)
+            assert rc == 0
+            assert np.array_equal(eic.to_host_u32(dist), og.dijkstra(int(s))[0])
+            for r in info["trace"]:
+                if r["flags"] & eic.STEP_PULL:
+                    kinds.add("swept" if r["flags"] & eic.STEP_SWEPT else "listed")
+    assert kinds == {"swept", "listed"}, kinds
 
 
 def test_parent_output():
