@@ -68,12 +68,39 @@ def dist_env():
 
 # DRAM bytes (read + write) of one query-kernel launch on the default workload,
 # from an ncu capture (profiles/k_eic_kron25_launches.md), valid only for the
-# kernel sources it was taken on; any change to them reports null.
+# kernel code it was taken on: the key hashes the kernel sources without their
+# comments and blank lines, and any change to the code reports null.
 KERNEL_SOURCES = ("paper_2506_19349_gb300/csrc/sssp.cu", "paper_2506_19349_gb300/csrc/common.cuh",
                   "paper_2506_19349_gb300/csrc/graph.h", "paper_2506_19349_gb300/csrc/stats.cuh", "include/eic.h")
-MEASURED_TRAFFIC = {  # {(scale, sources sha256): bytes per launch}
-    (25, "fb914f4fd0a64cbf6d150669de3673a45e6fdae6ee80efc3facd7f21404d0ba8"): 6442126464,
+MEASURED_TRAFFIC = {  # {(scale, kernel code sha256): bytes per launch}
+    (25, "1c2dac018fed4f62cc3fda40004e27154c122277b561edab06530623ae074580"): 6442126464,
 }
+
+
+def strip_c_comments(text):
+    """C/C++ source without // and /* */ comments (string and character
+    literals kept), trailing blanks and empty lines."""
+    out, i, n = [], 0, len(text)
+    while i < n:
+        c = text[i]
+        if c in "\"'":
+            j = i + 1
+            while j < n and text[j] != c:
+                j += 2 if text[j] == "\\" else 1
+            out.append(text[i:j + 1])
+            i = j + 1
+        elif text.startswith("//", i):
+            j = text.find("\n", i)
+            i = n if j < 0 else j
+        elif text.startswith("/*", i):
+            j = text.find("*/", i + 2)
+            out.append(" ")
+            i = n if j < 0 else j + 2
+        else:
+            out.append(c)
+            i += 1
+    lines = (line.rstrip() for line in "".join(out).split("\n"))
+    return "\n".join(line for line in lines if line)
 
 
 def kernel_sources_sha256():
@@ -81,8 +108,8 @@ def kernel_sources_sha256():
 
     h = hashlib.sha256()
     for rel in KERNEL_SOURCES:
-        with open(os.path.join(ROOT, rel), "rb") as f:
-            h.update(f.read())
+        with open(os.path.join(ROOT, rel), encoding="utf-8") as f:
+            h.update(strip_c_comments(f.read()).encode())
     return h.hexdigest()
 
 

@@ -8,12 +8,12 @@
 //   dist[ni]     distances in internal ids (non-isolated vertices by degree,
 //                densest first), u32, +inf = 0xFFFFFFFF, updated by atomicMin;
 //                copied to the caller's buffer in the original numbering at the end
-//   fbits[2][n]  frontier bitmaps by round parity: the SAP of Algorithm 1 inserts a
-//                vertex into the next frontier only if its bit was clear
+//   fbits[2][n/32]  frontier bitmaps by round parity: the SAP of Algorithm 1 inserts
+//                a vertex into the next frontier only if its bit was clear
 //   cursor[n]    where the last window relaxed from a vertex ended (offset in its row)
 //   q[2][n]      frontier queues, one per round parity
-//   sid/sd/scur  settled list in settling order (vertex, final distance, window
-//                cursor); step k owns [step_off[k], step_off[k+1])
+//   sid/sd/scur/srow  settled list in settling order (vertex, final distance,
+//                window cursor, row bounds); step k owns [step_off[k], step_off[k+1])
 //   touched[n]   first-step insertions (the first step's ub shrinks, so its
 //                tentative distances >= the final ub are reset to +inf)
 //   sbits[n/32]  settled bitmap: the pull set of Function 1 is the unsettled part of
@@ -25,11 +25,14 @@
 //
 // Phases (one grid barrier each): a round (the first round of a step runs
 // Function 1's push set and pull), an optional task phase, and per step one
-// statistics pass whose last block evaluates Eq. 1-3 and Function 2 and
-// publishes the next <st, lb, ub>. A round hands out chunks of blockDim items
-// to blocks (the first statically, then by an atomic counter); a block finds
-// each item's window in the weight-sorted row and relaxes the concatenation of
-// its chunk's windows with all its threads.
+// statistics pass after which block 0 evaluates Eq. 1-3 and Function 2 and
+// publishes the next <st, lb, ub>. In a round each warp takes 32 items at a
+// time (warp-strided, its next items' records loaded ahead); each lane finds
+// its item's window in the weight-sorted row, and the warp relaxes the
+// concatenation of its lanes' windows, windows longer than heavy_min becoming
+// 64-entry tasks for the task phase. A pull set of at least half the vertices
+// is swept in vertex order over the unsettled vertices only, compacted from
+// the settled bitmap 512 vertices at a time.
 #include <stdlib.h>
 #include <string.h>
 
@@ -399,12 +402,16 @@ __device__ __forceinline__ void on_success(const KArgs& A, const RoundCtx& R, bo
 
 // One round over nitems items. Items are frontier vertices (queue qin), or in
 // a step's first round Function 1's push set (a settled-list range), its pull
-// set (a prefix of the weight-ordered non-isolated vertices) and, once, the
-// source. Warp by warp without block synchronisation, each lane finds its
-// item's window in the weight-sorted row; windows up to heavy_min entries are
-// relaxed by the warp over their concatenation, longer ones become grid tasks.
-// A pull reads the prefix of its vertex's row with weight < ub - st.
-// List appends are staged in shared memory and flushed once per block.
+// set and, once, the source. The pull set is a prefix of the weight-ordered
+// non-isolated vertices (listed), or, when that prefix holds at least half of
+// them, every unsettled vertex (swept in vertex order). Warp by warp without
+// block synchronisation, each lane finds its item's window in the
+// weight-sorted row; windows up to heavy_min entries are relaxed by the warp
+// over their concatenation, kRelaxIlp entries per lane at a time, longer ones
+// become grid tasks. A pull reads the prefix of its vertex's row with weight
+// < ub - st: its first kPullFast entries in the lane, the rest by the warp.
+// Next-frontier and settled-list appends are staged per warp in shared
+// memory; tasks per block.
 template <uint32_t kPullFast, uint32_t kRelaxIlp>
 __device__ void round_phase(const KArgs& A, const RoundCtx& R, const Local& L, RoundScr& S, Stage& T,
                             uint32_t nitems, bool round1, const uint32_t* qin, Counters& C) {

@@ -2,6 +2,7 @@
 import ctypes
 import os
 import re
+import sys
 
 import pytest
 
@@ -123,3 +124,20 @@ def test_ctypes_mirrors_match_the_c_layout(tmp_path):
         assert int(got[st]) == ctypes.sizeof(cls), st
         for f in fields:
             assert int(got[f"{st}.{f}"]) == getattr(cls, f).offset, f"{st}.{f}"
+
+
+def test_traffic_key_ignores_comments_only():
+    """The bench's measured-traffic key hashes kernel code without comments:
+    comment and blank-line edits keep it, code edits change it, and comment
+    markers inside string literals are code."""
+    sys.path.insert(0, ROOT)
+    import bench
+
+    strip = bench.strip_c_comments
+    base = 'int f(int x) {\n  return x + 1;  // add one\n}\n'
+    assert strip(base) == strip('/* header */\nint f(int x) {\n\n  return x + 1;\n}  // end\n')
+    assert strip(base) != strip(base.replace("x + 1", "x + 2"))
+    code = 'asm("ld.global // not a comment /* nor this */ %0;" : "=r"(v));'
+    assert strip(code) == code
+    assert strip("char c = '/'; // tail") == "char c = '/';"
+    assert strip('s = "a\\"//b"; // c') == 's = "a\\"//b";'
