@@ -699,6 +699,10 @@ __device__ void round_phase(const KArgs& A, const RoundCtx& R, const Local& L, R
 }
 
 // The round's tasks, one warp per task of at most 64 entries.
+// With kAhead, a warp loads its next task while it runs the current one and
+// relaxes a push task's two entries per lane with their loads in flight
+// together (the single-query kernel's shape).
+template <bool kAhead>
 __device__ void task_phase(const KArgs& A, const RoundCtx& R, uint32_t ntasks, Stage& T, Counters& C) {
   const uint32_t lane = lane_id();
   const uint32_t wpb = blockDim.x >> 5;
@@ -706,10 +710,47 @@ __device__ void task_phase(const KArgs& A, const RoundCtx& R, uint32_t ntasks, S
   WarpList Qw = {T.wq[threadIdx.x >> 5], 0u, R.qcnt_out, R.qout};
   WarpList Fw = {T.wf[threadIdx.x >> 5], 0u, R.first_cnt, R.first_list};
   const int64_t pull_bound = R.ub - R.st;
-  for (uint32_t t = qblock(A) * wpb + (threadIdx.x >> 5); t < ntasks; t += nwarps) {
-    const uint4 tv = ld_list4(&A.tasks[t]);
+  const uint32_t t0 = qblock(A) * wpb + (threadIdx.x >> 5);
+  uint4 tnext = make_uint4(0u, 0u, 0u, 0u);
+  if constexpr (kAhead) {
+    if (t0 < ntasks) tnext = ld_list4(&A.tasks[t0]);
+  }
+  for (uint32_t t = t0; t < ntasks; t += nwarps) {
+    uint4 tv;
+    if constexpr (kAhead) {
+      tv = tnext;
+      if (t + nwarps < ntasks) tnext = ld_list4(&A.tasks[t + nwarps]);
+    } else {
+      tv = ld_list4(&A.tasks[t]);
+    }
     const Task tk = {tv.x, tv.y, tv.z, tv.w};
-    if (tk.d != kNone) {  // push
+    if (kAhead && tk.d != kNone) {  // push, both entries' loads in flight together
+      uint2 ent[2];
+      uint32_t dv[2], nd[2], old[2];
+      bool act[2], ok[2];
+#pragma unroll
+      for (uint32_t h = 0; h < 2; ++h) {
+        act[h] = lane + 32 * h < tk.len;
+        ent[h] = act[h] ? ld_stream(&A.G.adj[tk.beg + lane + 32 * h]) : make_uint2(0u, 0u);
+      }
+#pragma unroll
+      for (uint32_t h = 0; h < 2; ++h) dv[h] = act[h] ? __ldcg(&A.dist[ent[h].x]) : 0u;
+#pragma unroll
+      for (uint32_t h = 0; h < 2; ++h) {
+        ok[h] = false;
+        old[h] = 0;
+        nd[h] = tk.d + ent[h].y;
+        if (act[h]) {
+          C.trav += 1;
+          if (nd[h] < dv[h]) {
+            old[h] = atomicMin(&A.dist[ent[h].x], nd[h]);
+            ok[h] = nd[h] < old[h];
+          }
+        }
+      }
+#pragma unroll
+      for (uint32_t h = 0; h < 2; ++h) on_success(A, R, ok[h], ent[h].x, nd[h], old[h], C, Qw, Fw);
+    } else if (tk.d != kNone) {  // push
 #pragma unroll
       for (uint32_t h = 0; h < 2; ++h) {
         const uint32_t j = lane + 32 * h;
@@ -1161,7 +1202,7 @@ __device__ void run_query(const KArgs& A, QueryShared& Q, uint32_t& gen) {
       __syncthreads();
       if (hp != 0) {
         if (qb == 0 && threadIdx.x == 0) tl_mark(A, 9, (uint32_t)hp);  // diagnostic: the round's tasks
-        task_phase(A, R, (uint32_t)hp, T, C);
+        task_phase<(kRelaxIlp >= 2)>(A, R, (uint32_t)hp, T, C);
         if (!grid_barrier(&c->bar, &gen, A.nb, A.max_spin, &c->status)) {
           alive = false;
           break;
@@ -1204,12 +1245,24 @@ __device__ void run_query(const KArgs& A, QueryShared& Q, uint32_t& gen) {
       unsigned long long bdeg = 0;
       uint32_t bmax = 0, bany = 0;
       const uint32_t nthreads = A.nb * blockDim.x;
+      uint32_t xnext = 0;  // the single-query shape loads the next list entry one iteration ahead
+      if constexpr (kRelaxIlp >= 2) {
+        if (lbeg + qb * blockDim.x + threadIdx.x < lend) xnext = ld_list(&list[lbeg + qb * blockDim.x + threadIdx.x]);
+      }
       for (uint32_t base = lbeg + qb * blockDim.x; base < lend; base += nthreads) {
         const uint32_t idx = base + threadIdx.x;
         bool take = false;
         uint32_t x = 0, d = 0, xrb = 0, xre = 0;
+        uint32_t xcur = 0;
+        if constexpr (kRelaxIlp >= 2) {
+          xcur = xnext;
+          if (idx + nthreads < lend) xnext = ld_list(&list[idx + nthreads]);
+        }
         if (idx < lend) {
-          x = ld_list(&list[idx]);
+          if constexpr (kRelaxIlp >= 2)
+            x = xcur;
+          else
+            x = ld_list(&list[idx]);
           d = __ldcg(&A.dist[x]);
           xrb = __ldg(&A.G.row[x]);
           xre = __ldg(&A.G.row[x + 1]);
