@@ -24,9 +24,9 @@ struct Ctl {
   int64_t lb, ub, st, lb0;
   uint32_t step, done;
   uint32_t s_int;  // internal id of the source (0xFFFFFFFF: isolated source)
-  uint32_t push_beg, push_end;  // settled-list range pushed in round 1
+  uint32_t push_beg, push_end;  // settled-list range pushed in the step's first round
   uint32_t pull_on, pull_cnt, extra_s;
-  uint32_t pull_sweep;  // the pull set is swept in vertex order (pull_cnt = all vertices)
+  uint32_t pull_sweep;  // the pull set is swept in vertex order (pull_cnt = all vertices; the round takes the unsettled ones)
   uint32_t step_off_cur;  // settled-list offset where the current step's vertices start
   // private to the step-boundary block
   int64_t st0, st1, gap_lb;
