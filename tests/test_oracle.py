@@ -423,3 +423,20 @@ def test_eic_paper_bands_on_kron():
         assert tot["frontier"] / reach <= bands["nfrontier_max"]
         assert bands["ntrav_min"] <= tot["traversed"] / reach <= bands["ntrav_max"]
         assert tot["traversed"] < g.m  # fewer traversals than Dijkstra's |E| (Section 4.4)
+
+
+def test_oracle_traces_equal_the_golden_file():
+    """The oracle's Algorithm 1 step traces on the fixture workloads equal the
+    stored ones (golden/eic_traces.txt, written by golden/make_golden.py): any
+    change to the oracle's arithmetic shows up here and must come with a
+    regenerated file."""
+    import importlib.util
+
+    spec = importlib.util.spec_from_file_location("make_golden", os.path.join(GOLDEN, "make_golden.py"))
+    mg = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mg)
+    with open(os.path.join(GOLDEN, "eic_traces.txt")) as f:
+        want = [tuple(line.split()) for line in f if line.strip() and not line.startswith("#")]
+    got = [tuple(str(v) for v in row) for row in mg.traces()]
+    assert len(want) > 40
+    assert got == want
