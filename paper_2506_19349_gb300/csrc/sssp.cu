@@ -425,11 +425,10 @@ __device__ void round_phase(const KArgs& A, const RoundCtx& R, const Local& L, R
   WarpScr& W = S.w[warp];
   WarpList Qw = {T.wq[warp], 0u, R.qcnt_out, R.qout};
   WarpList Fw = {T.wf[warp], 0u, R.first_cnt, R.first_list};
-  // an item's record: the vertex (frontier, source), {dist, row begin, row
-  // end} (push set, from the settled list) or the pull-list entry. The next
-  // iteration's record is loaded while this iteration runs.
-  // A frontier vertex's record {vertex, dist, row begin, row end} is loaded
-  // one iteration ahead, its queue entry two iterations ahead.
+  // An item's record: {vertex, dist, row begin, row end} for a frontier
+  // vertex or the source, {dist, row begin, row end} for the push set (from
+  // the settled list), the nz entry for a listed pull. Records are loaded one
+  // warp iteration ahead, a frontier vertex's queue entry two ahead.
   auto fetch_id = [&](uint32_t ii) -> uint32_t { return !round1 && ii < nlisted ? ld_list(&qin[ii]) : 0u; };
   auto fetch = [&](uint32_t ii, uint32_t id) -> uint4 {
     if (ii >= nlisted) return make_uint4(0u, 0u, 0u, 0u);
