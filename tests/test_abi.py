@@ -141,3 +141,24 @@ def test_traffic_key_ignores_comments_only():
     assert strip(code) == code
     assert strip("char c = '/'; // tail") == "char c = '/';"
     assert strip('s = "a\\"//b"; // c') == 's = "a\\"//b";'
+
+
+def test_product_path_never_imports_the_oracle():
+    """Importing the package, its binding, its generators and build step (in a
+    fresh interpreter) loads nothing from oracle/; and no product source
+    imports it or loads its library."""
+    import subprocess
+
+    code = ("import sys; sys.path.insert(0, %r)\n"
+            "import paper_2506_19349_gb300, paper_2506_19349_gb300.binding, paper_2506_19349_gb300.build\n"
+            "import paper_2506_19349_gb300.graphgen\n"
+            "print(any(m == 'oracle' or m.startswith('oracle.') for m in sys.modules))\n") % ROOT
+    out = subprocess.run([sys.executable, "-c", code], check=True, capture_output=True, text=True).stdout.strip()
+    assert out == "False"
+    pkg = os.path.join(ROOT, "paper_2506_19349_gb300")
+    for base, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h", ".c")):
+                with open(os.path.join(base, f), encoding="utf-8") as fh:
+                    assert not re.search(r"^\s*(import|from)\s+oracle\b|liboracle|oracle/", fh.read(), re.M), \
+                        os.path.join(base, f)
