@@ -44,7 +44,8 @@ typedef struct eic_graph eic_graph;
  * (Section 4.1): alpha = 3, beta = 0.9, ST_NUM = 1024; RATIO_NUM is fixed at
  * EIC_RATIO_NUM when the graph is created.
  *   alpha, beta   Eq. 1-3 constants (beta in (0, 1)).
- *   st_num        size of the Function 2 candidate grid (Section 4.1), >= 1.
+ *   st_num        size of the Function 2 candidate grid (Section 4.1), in
+ *                 [1, 65536].
  *   gap_shift     step-width multiplier 2^gap_shift applied to Eq. 3's gap
  *                 (0 = the paper; any value keeps distances exact).
  *   block_threads threads per block of the relaxation kernel (0 = library
@@ -159,6 +160,17 @@ int eic_graph_info(const eic_graph* g, uint32_t* n, uint64_t* m, uint32_t* max_d
 /* Copy the CSR to host arrays: row_ptr[n+1] (uint64), nbr[2m], w[2m]; and
  * RtoW[EIC_RATIO_NUM] when rtow is non-NULL. Any array may be NULL. */
 int eic_graph_export(const eic_graph* g, uint64_t* row_ptr, uint32_t* nbr, uint32_t* w, uint32_t* rtow);
+
+/* Copy the CSR as the queries read it on the device, in internal vertex ids
+ * 0..ni-1 (the vertices of degree >= 1 ordered by degree descending, then
+ * original id): *ni = ni; int2orig[ni] maps an internal id to the caller's id;
+ * row[ni+1] (uint32) row offsets; nbr[2m] internal neighbour ids and w[2m]
+ * weights, each row sorted by (weight, the neighbour's original id): the
+ * weight order is what the window searches of the relaxation rely on
+ * (Section 4.1 sorts rows by weight). Any output may be NULL; host arrays,
+ * caller-owned. */
+int eic_graph_export_internal(const eic_graph* g, uint32_t* ni, uint32_t* int2orig, uint32_t* row, uint32_t* nbr,
+                              uint32_t* w);
 
 /* Device bytes held by the graph and by its query workspace. */
 int eic_graph_memory(const eic_graph* g, uint64_t* graph_bytes, uint64_t* workspace_bytes);
@@ -367,7 +379,7 @@ int eic_server_destroy(eic_server* s);
  * Same result as eic_sssp (exact distances, paper's default parameters), but
  * the query's scratch (frontier queues, settled list, statistics, tasks,
  * control block) lives in one fixed-size device array inside libeic instead of
- * the graph's workspace. That array (about 13 MB) is held on every GPU where
+ * the graph's workspace. That array (about 15.5 MB) is held on every GPU where
  * the library is loaded, until the process exits. The call allocates nothing:
  * no cudaMalloc, cudaFree or allocating library routine; the caller supplies
  * the graph (created beforehand with eic_graph_create) and the output buffer.

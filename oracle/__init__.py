@@ -16,7 +16,8 @@ Functions and the passages of the paper (arXiv 2506.19349) they follow:
     Floyd-Warshall, closed forms and the invariant checker).
   - ``bellman_ford`` / ``floyd_warshall``: the classical algorithms of
     Section 2.2 on the raw tuple list (tiny inputs).
-  - ``Graph.check``: invariant certificate of a distance array.
+  - ``Graph.check``: invariant certificate of a distance array
+    (``check_many``: the same over several arrays on host threads).
   - ``rtow``: maxW(G, ratio) quantile table RtoW (Section 3, Section 4.1).
   - ``highd``: highD over a degree multiset (Section 3).
   - ``gap``: Eq. 1-3. ``profit``: Eq. 4-6 with the clamping of Section 3.2.
@@ -194,6 +195,16 @@ class Graph:
         bad = ctypes.c_uint32(0)
         rc = _load().og_check(self._h, int(s), d.ctypes.data, ctypes.byref(bad))
         return int(rc), int(bad.value)
+
+    def check_many(self, sources, dists, nthreads: int | None = None) -> list[tuple[int, int]]:
+        """check() of each (sources[i], dists[i]) on host threads (the C call
+        releases the interpreter lock, so the checks run in parallel)."""
+        from concurrent.futures import ThreadPoolExecutor
+
+        pairs = list(zip(sources, dists))
+        nt = max(1, min(len(pairs), nthreads or os.cpu_count() or 1))
+        with ThreadPoolExecutor(nt) as ex:
+            return list(ex.map(lambda p: self.check(int(p[0]), p[1]), pairs))
 
     def parent(self, s: int, dist) -> np.ndarray:
         d = _u32(dist)

@@ -19,12 +19,16 @@ LIB_PATH = os.path.join(_HERE, "libeic.so")
 EIC_INF = 0xFFFFFFFF
 RATIO_NUM = 4096
 OK, EINVAL, ENOMEM, ECUDA, EOVERFLOW, ETIMEOUT, EBUSY, ESIZE, EABORT = range(9)
-NOALLOC_MAX_VERTICES = 1 << 18
+NOALLOC_MAX_VERTICES = 1 << 18  # the EIC_NOALLOC_* limits of include/eic.h
+NOALLOC_MAX_ENTRIES = 1 << 22
+NOALLOC_MAX_WEIGHT = 65535
+NOALLOC_MAX_DEGREES = 4096
+NOALLOC_MAX_STEPS = 1 << 14
 FLAG_NO_PULL = 1
 
 # Every name declared in include/eic.h.
 EXPORTS = ("eic_params_default", "eic_strerror", "eic_version", "eic_graph_create", "eic_graph_info",
-           "eic_graph_export", "eic_graph_memory", "eic_graph_destroy", "eic_sssp", "eic_sssp_batch",
+           "eic_graph_export", "eic_graph_export_internal", "eic_graph_memory", "eic_graph_destroy", "eic_sssp", "eic_sssp_batch",
            "eic_sssp_noalloc", "eic_batch_create", "eic_batch_run", "eic_batch_wait", "eic_batch_tune",
            "eic_batch_info", "eic_batch_destroy", "eic_server_create", "eic_server_submit", "eic_server_poll",
            "eic_server_wait", "eic_server_result", "eic_server_release", "eic_server_stats",
@@ -111,6 +115,8 @@ def load_library(path: str | None = None):
         L.eic_graph_info.restype = c_int
         L.eic_graph_export.argtypes = [vp, vp, vp, vp, vp]
         L.eic_graph_export.restype = c_int
+        L.eic_graph_export_internal.argtypes = [vp, ctypes.POINTER(u32), vp, vp, vp, vp]
+        L.eic_graph_export_internal.restype = c_int
         L.eic_graph_memory.argtypes = [vp, ctypes.POINTER(u64), ctypes.POINTER(u64)]
         L.eic_graph_memory.restype = c_int
         L.eic_graph_destroy.argtypes = [vp]
@@ -247,6 +253,21 @@ class Graph:
         _check(load_library().eic_graph_export(self._h, row.ctypes.data, nbr.ctypes.data, w.ctypes.data,
                                                rt.ctypes.data), "eic_graph_export")
         return row, nbr, w, rt
+
+    def export_internal(self):
+        """The CSR in the device's internal order: (int2orig uint32[ni], row
+        uint32[ni+1], nbr uint32[2m] internal ids, w uint32[2m])."""
+        L = load_library()
+        ni = ctypes.c_uint32()
+        _check(L.eic_graph_export_internal(self._h, ctypes.byref(ni), None, None, None, None),
+               "eic_graph_export_internal")
+        i2o = np.empty(ni.value, dtype=np.uint32)
+        row = np.empty(ni.value + 1, dtype=np.uint32)
+        nbr = np.empty(2 * self.m, dtype=np.uint32)
+        w = np.empty(2 * self.m, dtype=np.uint32)
+        _check(L.eic_graph_export_internal(self._h, ctypes.byref(ni), i2o.ctypes.data, row.ctypes.data,
+                                           nbr.ctypes.data, w.ctypes.data), "eic_graph_export_internal")
+        return i2o, row, nbr, w
 
     def memory(self):
         gb, wb = ctypes.c_uint64(), ctypes.c_uint64()

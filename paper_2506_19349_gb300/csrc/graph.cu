@@ -698,6 +698,39 @@ int eic_graph_export(const eic_graph* g, uint64_t* row_ptr, uint32_t* nbr, uint3
   return rc;
 }
 
+int eic_graph_export_internal(const eic_graph* g, uint32_t* ni, uint32_t* int2orig, uint32_t* row, uint32_t* nbr,
+                              uint32_t* w) {
+  if (!g) return EIC_EINVAL;
+  if (ni) *ni = g->dg.ni;
+  if (!int2orig && !row && !nbr && !w) return EIC_OK;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaSetDevice(g->device);
+  int rc = EIC_OK;
+  const uint64_t n_int = g->dg.ni, E = g->dg.two_m;
+  if (int2orig && n_int && cudaMemcpy(int2orig, g->int2orig, n_int * 4, cudaMemcpyDeviceToHost) != cudaSuccess)
+    rc = EIC_ECUDA;
+  if (rc == EIC_OK && row && cudaMemcpy(row, g->row, (n_int + 1) * 4, cudaMemcpyDeviceToHost) != cudaSuccess)
+    rc = EIC_ECUDA;
+  if (rc == EIC_OK && (nbr || w) && E) {
+    uint2* adj = (uint2*)malloc(E * sizeof(uint2));
+    if (!adj) {
+      rc = EIC_ENOMEM;
+    } else if (cudaMemcpy(adj, g->adj, E * sizeof(uint2), cudaMemcpyDeviceToHost) != cudaSuccess) {
+      rc = EIC_ECUDA;
+    } else {
+      for (uint64_t k = 0; k < E; ++k) {
+        if (nbr) nbr[k] = adj[k].x;
+        if (w) w[k] = adj[k].y;
+      }
+    }
+    free(adj);
+  }
+  (void)cudaGetLastError();
+  cudaSetDevice(dev);
+  return rc;
+}
+
 int eic_graph_memory(const eic_graph* g, uint64_t* graph_bytes, uint64_t* workspace_bytes) {
   if (!g) return EIC_EINVAL;
   if (graph_bytes) *graph_bytes = g->bytes;

@@ -121,6 +121,9 @@ struct SlotPool {
   }
 };
 
+// Ring of settled degree sums for Function 2: 2^bits slots, one per distance
+// while maxW < 2^20; wider weights get *shift > 0 and 2^20 slots, which then
+// hold Function 2's candidate bins (summed exactly from the settled list).
 inline uint32_t ring_layout(uint32_t maxw, uint32_t* shift) {
   const uint32_t m = maxw ? maxw : 1;
   uint32_t bits = 0;

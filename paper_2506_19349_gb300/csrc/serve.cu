@@ -314,7 +314,8 @@ int eic_server_create(const eic_graph* const* graphs, uint32_t num_graphs, const
   eic_params pr;
   eic_params_default(&pr);
   if (params) pr = *params;
-  if (!(pr.beta > 0.0 && pr.beta < 1.0) || pr.st_num == 0 || pr.gap_shift > 16) return EIC_EINVAL;
+  if (!(pr.beta > 0.0 && pr.beta < 1.0) || pr.st_num == 0 || pr.st_num > 65536 || pr.gap_shift > 16)
+    return EIC_EINVAL;
   if (pr.block_threads != 0 && (pr.block_threads % 32 != 0 || pr.block_threads < 128 || pr.block_threads > 512))
     return EIC_EINVAL;
   if (pr.heavy_min == 0) pr.heavy_min = 32;

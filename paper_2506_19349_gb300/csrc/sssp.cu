@@ -20,7 +20,8 @@
 //                a prefix of the non-isolated vertices ordered by smallest row weight
 //   hist[D]      unsettled vertices per distinct degree (for highD)
 //   ring[R]      degree sums of settled vertices by distance mod R (for the
-//                sumD differences of Function 2's candidates)
+//                sumD differences of Function 2's candidates, while maxW < 2^20;
+//                wider weights sum them exactly from the settled list)
 //   tasks[]      windows longer than heavy_min, cut into 64-entry tasks for the grid
 //
 // Phases (one grid barrier each): a round (the first round of a step runs
@@ -169,10 +170,13 @@ struct S2Scr {
   unsigned long long ring[kShRing];
 };
 
+constexpr uint32_t kStBins = 1920;  // Function 2 candidate bins held in shared memory (ST_NUM + 2 at most)
+
 struct S3Scr {
   unsigned long long part[kMaxBlock];
   double bp[32];
   uint32_t bk[32];
+  unsigned long long bins[kStBins];
 };
 
 union PhaseScr {
@@ -803,20 +807,53 @@ __device__ void task_phase(const KArgs& A, const RoundCtx& R, uint32_t ntasks, S
 
 // Function 2 for the boundary <lb, ub> -> next pair <ub, ub + gap(ub)>, run by
 // one whole block. Candidates x_k = st0 + floor(k (st1 - st0) / ST_NUM) < ub;
-// D(x') = sumD(x') - sumD(ub) from the ring of settled degree sums.
+// D(x') = sumD(x') - sumD(ub), the degree sum of the settled vertices with
+// x' <= dist < ub, where x' >= wl = max(ub - maxW, 0). While maxW < 2^20 it is
+// read from the ring of settled degree sums (one slot per distance). For wider
+// weights it is summed exactly from the settled list entries [sbeg, send)
+// (the steps that end above wl): a vertex at distance d >= wl adds its degree
+// to bin 1 + k_d, k_d the last k with x_k <= d (-1 if none), so that D(x_k) is
+// the sum of the bins from 1 + k, and D(wl) of all of them.
 __device__ int64_t block_compute_st(const KArgs& A, S3Scr& S, int64_t ub, uint64_t sumd_ub, int64_t gap_lb,
-                                    int64_t gap_ub_raw, int64_t y, int64_t st0, int64_t st1) {
+                                    int64_t gap_ub_raw, int64_t y, int64_t st0, int64_t st1, uint32_t sbeg,
+                                    uint32_t send) {
   const int64_t maxw = A.G.maxw;
   if (sumd_ub >= A.G.m || gap_lb == maxw) return ub;
   if (gap_ub_raw == maxw) return ub - maxw;
   const uint32_t t = threadIdx.x, nt = blockDim.x;
   const int64_t wl = ub - maxw > 0 ? ub - maxw : 0;
-  const uint32_t sh = A.ring_shift;
-  const uint64_t sl = (uint64_t)wl >> sh, su = (uint64_t)(ub - 1) >> sh;
-  const uint64_t L = su - sl + 1;  // ring slots covering [wl, ub)
+  const bool by_ring = A.ring_shift == 0;
+  const uint64_t nbins = (uint64_t)A.st_num + 2;
+  const bool sh_bins = nbins <= kStBins;
+  unsigned long long* bins = sh_bins ? S.bins : A.ring;  // the ring (2^20 slots) is unused for wide weights
+  if (!by_ring) {
+    for (uint64_t q = t; q < nbins; q += nt) bins[q] = 0ull;
+    __syncthreads();
+    const uint64_t span = (uint64_t)(st1 - st0);
+    for (uint32_t i = sbeg + t; i < send; i += nt) {
+      const int64_t d = ld_list(&A.sd[i]);
+      if (d < wl) continue;
+      const uint2 rr = ld_list2(&A.srow[i]);
+      uint64_t cnt;  // how many x_k are <= d: the k with k (st1 - st0) < (d - st0 + 1) ST_NUM
+      if (d < st0)
+        cnt = 0;
+      else if (span == 0)
+        cnt = nbins - 1;
+      else
+        cnt = min(((uint64_t)(d - st0 + 1) * A.st_num + span - 1) / span, nbins - 1);
+      atomicAdd(&bins[cnt], (unsigned long long)(rr.y - rr.x));
+    }
+    __syncthreads();
+  }
+  const uint64_t sl = by_ring ? (uint64_t)wl : 0, su = by_ring ? (uint64_t)(ub - 1) : nbins - 1;
+  auto slot = [&](uint64_t q) -> unsigned long long {
+    if (by_ring) return __ldcg(&A.ring[q & A.ring_mask]);
+    return sh_bins ? bins[q] : __ldcg(&bins[q]);
+  };
+  const uint64_t L = su - sl + 1;  // slots covering [wl, ub), or the bins
   const uint64_t cs = (L + nt - 1) / nt;
   unsigned long long mine = 0;
-  for (uint64_t q = sl + t * cs; q < sl + (t + 1) * cs && q <= su; ++q) mine += __ldcg(&A.ring[q & A.ring_mask]);
+  for (uint64_t q = sl + t * cs; q < sl + (t + 1) * cs && q <= su; ++q) mine += slot(q);
   S.part[t] = mine;
   __syncthreads();
   for (uint32_t o = 1; o < nt; o <<= 1) {  // suffix sums over chunks
@@ -835,10 +872,10 @@ __device__ int64_t block_compute_st(const KArgs& A, S3Scr& S, int64_t ub, uint64
       const int64_t xp = st0 + (int64_t)(((uint64_t)(k - 1) * (uint64_t)(st1 - st0)) / A.st_num);
       if ((xp > ub - maxw ? xp : ub - maxw) == xc) continue;
     }
-    const uint64_t q0 = (uint64_t)xc >> sh;
+    const uint64_t q0 = by_ring ? (uint64_t)xc : (x >= wl ? (uint64_t)k + 1 : 0);
     const uint64_t c = (q0 - sl) / cs;
     unsigned long long dsum = c + 1 < nt ? S.part[c + 1] : 0;
-    for (uint64_t q = q0; q < sl + (c + 1) * cs && q <= su; ++q) dsum += __ldcg(&A.ring[q & A.ring_mask]);
+    for (uint64_t q = q0; q < sl + (c + 1) * cs && q <= su; ++q) dsum += slot(q);
     const double p = dev_profit(x, ub, y, dsum, sumd_ub, A.G.maxw, A.G.two_m);
     if (p > best) {
       best = p;
@@ -957,14 +994,20 @@ __device__ void step_boundary(const KArgs& A, PhaseScr& P, BState& B, const Loca
     if (B.st1 < 0 && sumd_ub <= G.m) B.st1 = ub;
     sh_i[1] = gap_raw;
     sh_i[2] = gap_raw << A.gap_shift;
+    // the settled-list entries of the steps ending above ub - maxW (from the first such step on)
+    const int64_t wl = ub - (int64_t)G.maxw > 0 ? ub - (int64_t)G.maxw : 0;
+    uint32_t j = B.j0;
+    while (j <= k && __ldcg(&A.step_ub[j]) <= wl) ++j;
+    sh_u[2] = j <= k ? __ldcg(&A.step_off[j]) : sh_u[1];
   }
   __syncthreads();
   const int64_t gap_raw = sh_i[1], width = sh_i[2];
   const int64_t nlb = ub, nub = ub + width;
-  const int64_t nst = (A.flags & EIC_FLAG_NO_PULL)
-                          ? nlb
-                          : block_compute_st(A, P.s3, ub, sumd_ub, B.gap_lb, gap_raw, nub, B.st0, B.st1);
-  {  // zero the ring slots the next statistics pass fills: [max(nlb, nub - maxW), nub)
+  const int64_t nst = (A.flags & EIC_FLAG_NO_PULL) ? nlb
+                                                    : block_compute_st(A, P.s3, ub, sumd_ub, B.gap_lb, gap_raw, nub,
+                                                                       B.st0, B.st1, (uint32_t)sh_u[2],
+                                                                       (uint32_t)sh_u[1]);
+  if (A.ring_shift == 0) {  // zero the ring slots the next statistics pass fills: [max(nlb, nub - maxW), nub)
     const int64_t zl = nub - (int64_t)G.maxw > nlb ? nub - (int64_t)G.maxw : nlb;
     const uint64_t ql = (uint64_t)zl >> A.ring_shift, qu = (uint64_t)(nub - 1) >> A.ring_shift;
     for (uint64_t q = ql + threadIdx.x; q <= qu; q += blockDim.x) __stcg(&A.ring[q & A.ring_mask], 0ull);
@@ -1301,7 +1344,7 @@ __device__ void run_query(const KArgs& A, QueryShared& Q, uint32_t& gen) {
         // D(x) ring: in a narrow window the step's settled vertices share few
         // distances; then one atomic per distinct slot in the warp, with the
         // group's degree sum (32-bit while 32 degrees cannot overflow it)
-        const bool rk = take && (int64_t)d >= wlo;
+        const bool rk = take && (int64_t)d >= wlo && A.ring_shift == 0;  // (wide weights: Function 2 sums exactly)
         const uint32_t slot = rk ? (ring_sh ? (uint32_t)(d - wlo) : (uint32_t)(((uint64_t)d >> A.ring_shift) & A.ring_mask))
                                  : EIC_INF;
         if (ring_narrow) {
@@ -1829,6 +1872,7 @@ constexpr uint32_t kHeavyMinCeil = 4096;
 constexpr uint32_t kDefaultHeavyMin = 32;
 constexpr int kDefaultBlock = 512;
 constexpr uint32_t kDefaultSpinLog2 = 22;
+constexpr uint32_t kStNumMax = 1u << 16;  // Function 2's candidate bins fit the 2^20-slot ring of wide weights
 
 template <typename T>
 int walloc(Workspace* ws, T** p, uint64_t count) {
@@ -1849,7 +1893,7 @@ int resolve_params(const eic_params* in, eic_params* out) {
     eic_params_default(out);
   }
   if (!(out->beta > 0.0 && out->beta < 1.0)) return EIC_EINVAL;
-  if (out->st_num == 0) return EIC_EINVAL;
+  if (out->st_num == 0 || out->st_num > kStNumMax) return EIC_EINVAL;
   if (out->gap_shift > 16) return EIC_EINVAL;
   if (out->block_threads != 0 &&
       (out->block_threads % 32 != 0 || out->block_threads < 128 || out->block_threads > kMaxBlock))
@@ -2009,7 +2053,7 @@ int eic_ws_ensure(eic_graph* g, int) {
   uint32_t bits = 0;
   while (bits < 32 && (1ull << bits) <= maxw) ++bits;  // 2^bits > maxW
   w->ring_bits = bits < 20 ? bits : 20;
-  w->ring_shift = bits > 20 ? bits - 20 : 0;
+  w->ring_shift = bits > 20 ? bits - 20 : 0;  // nonzero: Function 2 sums exactly, the ring holds its bins
   // a window longer than heavy_min >= 16 yields ceil(len / 64) <= len / 16 tasks,
   // and the windows of one round belong to distinct vertices
   w->task_cap = (uint32_t)(G.two_m / kHeavyMinFloor + 2);
@@ -2648,6 +2692,7 @@ constexpr uint64_t kNaStepUb = kNaTaskOff + na_align(kNaTasks * sizeof(Task));
 constexpr uint64_t kNaStepOff = kNaStepUb + na_align((kNaS + 2) * 8);
 constexpr uint64_t kNaCtl = kNaStepOff + na_align((kNaS + 2) * 4);
 constexpr uint64_t kNaBytes = kNaCtl + na_align(sizeof(Ctl));
+static_assert(kNaBytes > 15000000 && kNaBytes < 16000000, "the header states the scratch size as about 15.5 MB");
 
 static __device__ __align__(256) unsigned char g_na_scratch[kNaBytes];
 
@@ -2743,18 +2788,27 @@ extern "C" int eic_sssp_noalloc(const eic_graph* gc, uint32_t source, uint32_t* 
   A.timeline = nullptr;
   A.timeline_cap = 0;
   A.nb = (uint32_t)nd.grid;
-  EIC_CUDA_TRY(cudaMemsetAsync(A.dist, 0xFF, (uint64_t)G.ni * 4, st));
-  EIC_CUDA_TRY(cudaMemsetAsync(A.sbits, 0, ((uint64_t)G.ni / 32 + 2) * 4, st));
-  EIC_CUDA_TRY(cudaMemsetAsync(A.fbits, 0, 2 * ((uint64_t)G.ni / 32 + 2) * 4, st));
-  k_init<<<64, 256, 0, st>>>(A);
-  EIC_CUDA_TRY(cudaGetLastError());
-  void* args[] = {&A};
-  EIC_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)k_eic, dim3(nd.grid), dim3(kDefaultBlock), args, 0, st));
-  k_output<<<4 * nd.grid, 256, 0, st>>>(G, A.dist, source, dist);
-  EIC_CUDA_TRY(cudaGetLastError());
+  // Once anything is enqueued, every return waits for the stream first: the
+  // next call may reuse the scratch only when this call's work has finished.
+  auto enqueue = [&]() -> int {
+    EIC_CUDA_TRY(cudaMemsetAsync(A.dist, 0xFF, (uint64_t)G.ni * 4, st));
+    EIC_CUDA_TRY(cudaMemsetAsync(A.sbits, 0, ((uint64_t)G.ni / 32 + 2) * 4, st));
+    EIC_CUDA_TRY(cudaMemsetAsync(A.fbits, 0, 2 * ((uint64_t)G.ni / 32 + 2) * 4, st));
+    k_init<<<64, 256, 0, st>>>(A);
+    EIC_CUDA_TRY(cudaGetLastError());
+    void* args[] = {&A};
+    EIC_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)k_eic, dim3(nd.grid), dim3(kDefaultBlock), args, 0, st));
+    k_output<<<4 * nd.grid, 256, 0, st>>>(G, A.dist, source, dist);
+    EIC_CUDA_TRY(cudaGetLastError());
+    return EIC_OK;
+  };
   int status = 0;
-  EIC_CUDA_TRY(cudaMemcpyAsync(&status, &ctl->status, sizeof(int), cudaMemcpyDeviceToHost, st));
-  EIC_CUDA_TRY(cudaStreamSynchronize(st));
+  rc = enqueue();
+  if (rc == EIC_OK && cudaMemcpyAsync(&status, &ctl->status, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+    rc = EIC_ECUDA;
+  if (cudaStreamSynchronize(st) != cudaSuccess && rc == EIC_OK) rc = EIC_ECUDA;
+  (void)cudaGetLastError();
+  if (rc) return rc;
   return status;
 }
 

@@ -213,6 +213,7 @@ def kron(scale: int, seed: int = 2, edgefactor: int = 16, weights: str = "unifor
     """RMAT scale/edgefactor graph, ids permuted, weights per unordered pair.
 
     weights: "uniform255" -> integers uniform in [1,255];
+             "uniform:W"  -> integers uniform in [1,W];
              "lognormal"  -> clamp(llround(exp(3 + 1.5 Z)), 1, 65535);
              "power:P"    -> the paper's power variant, Eq. 7 with power P;
              "pivot:Y"    -> the paper's pivot variant, Eq. 8 with pivot Y, as integers 1..65535.
@@ -223,6 +224,8 @@ def kron(scale: int, seed: int = 2, edgefactor: int = 16, weights: str = "unifor
     src, dst = rmat(scale, ne, seed, out_src=o.get("src"), out_dst=o.get("dst"))
     if weights == "uniform255":
         w = weights_uniform(src, dst, seed, 1, 255, out=o.get("w"))
+    elif weights.startswith("uniform:"):
+        w = weights_uniform(src, dst, seed, 1, int(weights[8:]), out=o.get("w"))
     elif weights == "lognormal":
         w = weights_lognormal(src, dst, seed, 3.0, 1.5, 1, 65535, out=o.get("w"))
     elif weights.startswith("power:"):

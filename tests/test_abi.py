@@ -162,3 +162,14 @@ def test_product_path_never_imports_the_oracle():
                 with open(os.path.join(base, f), encoding="utf-8") as fh:
                     assert not re.search(r"^\s*(import|from)\s+oracle\b|liboracle|oracle/", fh.read(), re.M), \
                         os.path.join(base, f)
+
+
+def test_binding_noalloc_limits_equal_the_header():
+    from paper_2506_19349_gb300 import binding
+
+    text = open(os.path.join(ROOT, "include", "eic.h")).read()
+    for name in ("VERTICES", "ENTRIES", "WEIGHT", "DEGREES", "STEPS"):
+        m = re.search(rf"#define EIC_NOALLOC_MAX_{name} \(?(1u << (\d+)|(\d+)u)\)?", text)
+        assert m, name
+        val = 1 << int(m.group(2)) if m.group(2) else int(m.group(3))
+        assert getattr(binding, f"NOALLOC_MAX_{name}") == val, name

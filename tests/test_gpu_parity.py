@@ -54,6 +54,10 @@ def _cases():
         yield f"kron12_power{p}", G.kron(12, seed=27, weights=f"power:{p}", nsources=2)
     for y in (0.1, 0.9):
         yield f"kron12_pivot{y}", G.kron(12, seed=28, weights=f"pivot:{y}", nsources=2)
+    # weights of 2^20 and above: Function 2 sums D(x') exactly from the settled list
+    for wmax, scale, seed in ((1 << 21, 12, 90), (1 << 24, 12, 90), (1 << 27, 13, 91)):
+        yield f"kron{scale}_uniform{wmax}", G.kron(scale, seed=seed, weights=f"uniform:{wmax}", nsources=3)
+    yield "kron13_power24", G.kron(13, seed=91, weights="power:24", nsources=3)
 
 
 CASES = list(_cases())
@@ -70,6 +74,32 @@ def test_csr_equals_oracle(name, wl):
     assert np.array_equal(rt, og.rtow())
     assert g.highd0 == O.highd(og.degrees())
     assert (g.m, g.max_w, g.max_deg) == (og.m, og.maxw, og.maxdeg)
+
+
+@pytest.mark.parametrize("name,wl", CASES, ids=[c[0] for c in CASES])
+def test_device_row_order(name, wl):
+    """The CSR as the kernels read it: internal ids are the non-isolated
+    vertices by (degree descending, original id), each row is strictly
+    increasing in (weight, the neighbour's original id) (the window searches
+    rely on the weight order of Section 4.1), and every row holds the
+    oracle's edges."""
+    g, og = _pair(wl)
+    i2o, row, nbr, w = g.export_internal()
+    orow, onbr, ow = og.csr()
+    deg = np.diff(orow).astype(np.int64)
+    want_ids = np.lexsort((np.arange(wl.n), -deg))[: int((deg > 0).sum())]
+    assert np.array_equal(i2o, want_ids.astype(np.uint32))
+    assert row[0] == 0 and row[-1] == nbr.size and np.all(np.diff(row.astype(np.int64)) >= 1)
+    assert np.array_equal(np.diff(row.astype(np.int64)), deg[i2o])
+    key = (w.astype(np.uint64) << np.uint64(32)) | i2o[nbr].astype(np.uint64)
+    inrow = np.ones(max(nbr.size - 1, 0), dtype=bool)  # entry pairs (k, k + 1) of the same row
+    inrow[row[1:-1].astype(np.int64) - 1] = False
+    assert np.all(key[1:][inrow] > key[:-1][inrow]), "a row is not sorted by (weight, original neighbour id)"
+    for i in range(0, i2o.size, max(1, i2o.size // 257)):  # rows back in the caller's ids, against the oracle
+        u = i2o[i]
+        got = sorted(zip(w[row[i]:row[i + 1]].tolist(), i2o[nbr[row[i]:row[i + 1]]].tolist()))
+        want = sorted(zip(ow[orow[u]:orow[u + 1]].tolist(), onbr[orow[u]:orow[u + 1]].tolist()))
+        assert got == want, (name, int(u))
 
 
 @pytest.mark.parametrize("name,wl", CASES, ids=[c[0] for c in CASES])

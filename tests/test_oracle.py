@@ -19,6 +19,7 @@ import pytest
 
 import oracle as O
 from paper_2506_19349_gb300 import graphgen as G
+from trace_check import check_trace_against_exact
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 
@@ -347,53 +348,8 @@ def test_eic_restatement_exact(name, wl):
 
 
 def _check_trace_against_exact(g, d, trace, tot):
-    """Every step quantity recomputed from the exact distances (Section 3)."""
-    rt = g.rtow()
-    deg = g.degrees()
-    highd0 = O.highd(deg)
-    fin = d != O.INF
-    hi = deg >= highd0
-    st0 = int(d[hi & fin].min()) if (hi & fin).any() else O.INF_T
-    assert trace[0]["lb"] == 0 and trace[0]["ub"] == st0 and tot["st0"] == st0
-    for k, row in enumerate(trace):
-        sumd, highd = g.stats_at(d, row["lb"])
-        assert (row["sumd_lb"], row["highd_lb"]) == (sumd, highd)
-        assert row["gap_lb"] == O.gap(sumd, highd, g.nnz, rt)[0]
-        if k > 0:
-            assert row["lb"] == trace[k - 1]["ub"]
-            assert row["ub"] == row["lb"] + row["gap_lb"]
-        if row["ub"] < O.INF_T:
-            assert row["settled"] == int(((d >= row["lb"]) & (d < row["ub"]) & fin).sum())
-    # termination rule of Algorithm 1: the first boundary with max lsp + maxW < lb
-    mx = int(d[fin].max())
-    assert mx + g.maxw < trace[-1]["ub"]
-    for row in trace[:-1]:
-        assert mx + g.maxw >= row["ub"]
-    # Function 2 at each boundary, from exact distances
-    m = g.nnz // 2
-    st1 = next((r["lb"] for r in trace[1:] if r["sumd_lb"] <= m), None)
-    cache = {}
-    for k in range(1, len(trace)):
-        ub, sumd_ub = trace[k]["lb"], trace[k]["sumd_lb"]
-        gap_lb, gap_ub = trace[k - 1]["gap_lb"], trace[k]["gap_lb"]
-        if sumd_ub >= m or gap_lb == g.maxw:
-            want = ub
-        elif gap_ub == g.maxw:
-            want = ub - g.maxw
-        else:
-            y = ub + gap_ub
-            want, best = ub, 0.0
-            for j in range(O.ST_NUM + 1):
-                x = st0 + (j * (st1 - st0)) // O.ST_NUM
-                if x >= ub:
-                    continue
-                xc = max(x, ub - g.maxw)
-                if (xc, ub) not in cache:
-                    cache[(xc, ub)] = g.degree_between(d, xc, ub)
-                p = O.profit(x, ub, y, cache[(xc, ub)], sumd_ub, g.maxw, g.nnz)
-                if best < p:
-                    best, want = p, x
-        assert trace[k]["st"] == want, k
+    assert tot["st0"] == trace[0]["ub"]
+    check_trace_against_exact(g, d, trace)
 
 
 def test_eic_random_small_graphs_exact():
@@ -440,3 +396,19 @@ def test_oracle_traces_equal_the_golden_file():
     got = [tuple(str(v) for v in row) for row in mg.traces()]
     assert len(want) > 40
     assert got == want
+
+
+def test_wide_weight_cases_reach_function2_profit():
+    """The GPU parity cases with weights of 2^20 and above (where Function 2
+    sums D(x') from the settled list) do evaluate Function 2's profits: some
+    step's st is a grid candidate, neither lb nor lb - maxW (Section 3.2)."""
+    for wmax, scale, seed in ((1 << 21, 12, 90), (1 << 24, 12, 90), (1 << 27, 13, 91)):
+        wl = G.kron(scale, seed=seed, weights=f"uniform:{wmax}", nsources=3)
+        g = O.Graph(wl.n, wl.src, wl.dst, wl.w)
+        assert g.maxw >= 1 << 20
+        for s in wl.sources:
+            d, rc = g.dijkstra(int(s))
+            de, rc2, trace, tot = g.eic(int(s))
+            assert rc == rc2 == 0 and (de == d).all()
+            assert any(r["st"] not in (r["lb"], r["lb"] - g.maxw) for r in trace[1:]), (wmax, int(s))
+            _check_trace_against_exact(g, d, trace, tot)
