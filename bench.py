@@ -67,9 +67,9 @@ def dist_env():
 
 
 # DRAM bytes (read + write) of one query-kernel launch on the default workload,
-# from an ncu capture (profiles/k_eic_kron25_launches.md), valid only for the
-# kernel code it was taken on: the key hashes the kernel sources without their
-# comments and blank lines, and any change to the code reports null.
+# from an ncu capture of dram__bytes_read.sum + dram__bytes_write.sum, valid only
+# for the kernel code it was taken on: the key hashes the kernel sources without
+# their comments and blank lines, and any change to the code reports null.
 KERNEL_SOURCES = ("paper_2506_19349_gb300/csrc/sssp.cu", "paper_2506_19349_gb300/csrc/common.cuh",
                   "paper_2506_19349_gb300/csrc/graph.h", "paper_2506_19349_gb300/csrc/stats.cuh", "include/eic.h")
 MEASURED_TRAFFIC = {  # {(scale, kernel code sha256): bytes per launch}
@@ -337,13 +337,13 @@ def batched_mixed(eic, torch, stream, runs):
     del wls
     dists = [eic.new_dist(g.n) for g in graphs]
 
-    def plain_pass():
+    def plain_pass(params=None):
         evs = []
-        for g, s, d in zip(graphs, srcs, dists):
+        for i, (g, s, d) in enumerate(zip(graphs, srcs, dists)):
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            eic.sssp(g, s, dist=d)
+            eic.sssp(g, s, dist=d, params=params[i] if params else None)
             e1.record(stream)
             evs.append((e0, e1))
         torch.cuda.synchronize()
@@ -363,24 +363,42 @@ def batched_mixed(eic, torch, stream, runs):
     t0 = time.perf_counter()
     cfg = b.tune(stream)
     tune_s = time.perf_counter() - t0
+    shifts = b.gap_shifts()
     batch_run_timed(b, stream, torch, 1)  # first run captures the CUDA graph
     ms = batch_run_timed(b, stream, torch, runs)
     same = all(np.array_equal(eic.to_host_u32(d), r) for d, r in zip(dists, ref))
     info = b.info()
     b.close()
+    # like for like: the plain path at the step width the tuner chose for each graph
+    tuned_params = [eic.default_params(gap_shift=sh) for sh in shifts]
+    plain_pass(tuned_params)  # warm-up
+    p0.record(stream)
+    lat_t = plain_pass(tuned_params)
+    p1.record(stream)
+    torch.cuda.synchronize()
+    plain_t_ms = p0.elapsed_time(p1)
+    same_t = all(np.array_equal(eic.to_host_u32(d), r) for d, r in zip(dists, ref))
     lat.sort()
+    lat_t.sort()
     plain_gteps = edges / (plain_ms * 1e-3) / 1e9
+    plain_t_gteps = edges / (plain_t_ms * 1e-3) / 1e9
     gteps = edges / (statistics.mean(ms) * 1e-3) / 1e9
+    pct = lambda v, q: v[min(len(v) - 1, int(q * len(v)))]
     return {"workload": "32 graphs: RMAT scales 12..22 (two seeds each) and grids 256^2 x3, 512^2 x3, 1024^2 x2, "
                         "2048^2 x2 (10% edges deleted, 2% diagonals), weights uniform [1,255], 8 sources each",
             "queries": len(srcs), "generate_s": gen_s,
-            "plain": {"value": plain_gteps, "unit": "GTEPS", "ms": plain_ms,
-                      "latency_ms": {"p50": lat[len(lat) // 2], "p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))]}},
+            "plain": {"value": plain_gteps, "unit": "GTEPS", "ms": plain_ms, "gap_shift": 0,
+                      "latency_ms": {"p50": pct(lat, 0.5), "p99": pct(lat, 0.99)}},
+            "plain_tuned": {"value": plain_t_gteps, "unit": "GTEPS", "ms": plain_t_ms,
+                            "gap_shift": "per graph, the batch tuner's choice", "identical_to_plain": same_t,
+                            "latency_ms": {"p50": pct(lat_t, 0.5), "p99": pct(lat_t, 0.99)}},
             "batched": {"value": gteps, "unit": "GTEPS", "ms_per_batch": statistics.mean(ms), "runs": runs,
-                        "tune_s": tune_s, "identical_to_plain": same,
+                        "tune_s": tune_s, "identical_to_plain": same, "gap_shifts": sorted(set(shifts)),
                         "config": {k: info[k] for k in ("groups", "blocks_per_group", "block_threads", "cuda_graph",
                                                         "gap_shift", "heavy_min", "scratch_bytes")}},
-            "speedup": gteps / plain_gteps}
+            "speedup": gteps / plain_t_gteps, "speedup_basis": "batched vs the plain path at the same per-graph "
+                                                               "step width (like for like)",
+            "speedup_vs_plain_default": gteps / plain_gteps}
 
 
 def stress(eic, torch, stream, nsources):
@@ -465,11 +483,23 @@ def serving(eic, torch, stream, rates, seconds_per_rate, max_per_rate):
         e1.synchronize()
         svc.append(e0.elapsed_time(e1))
     plain_qps = 1000.0 / statistics.mean(svc)
-    del dist
     srv = eic.Server(graphs)
     t0 = time.perf_counter()
     shifts = srv.tune([pools[g][0] for g in range(len(graphs))])  # per-graph step width (exact)
     tune_s = time.perf_counter() - t0
+    # like for like: the plain service time of each request at its graph's tuned step width
+    svc_t = []
+    for g, s in pool:
+        p = eic.default_params(gap_shift=shifts[g])
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        eic.sssp(graphs[g], s, dist=dist[g], params=p)
+        e1.record(stream)
+        e1.synchronize()
+        svc_t.append(e0.elapsed_time(e1))
+    plain_t_qps = 1000.0 / statistics.mean(svc_t)
+    del dist
     rows = []
     rng = np.random.default_rng(11)
     switch = sys.getswitchinterval()
@@ -512,20 +542,26 @@ def serving(eic, torch, stream, rates, seconds_per_rate, max_per_rate):
         th.join()
         wall = time.perf_counter() - start
         st = srv.stats()
-        # one at a time: request k starts when it has arrived and k-1 is done
-        fin, lat1 = 0.0, []
-        for k in range(n_req):
-            begin = max(arrive[k] * 1e3, fin)
-            fin = begin + svc[picks[k]]
-            lat1.append(fin - arrive[k] * 1e3)
-        lat1.sort()
+        def replay(times):  # one at a time: request k starts when it has arrived and k-1 is done
+            fin, lat1 = 0.0, []
+            for k in range(n_req):
+                begin = max(arrive[k] * 1e3, fin)
+                fin = begin + times[picks[k]]
+                lat1.append(fin - arrive[k] * 1e3)
+            lat1.sort()
+            return {"qps": n_req / (fin * 1e-3), "p50_ms": lat1[len(lat1) // 2],
+                    "p99_ms": lat1[min(len(lat1) - 1, int(0.99 * len(lat1)))]}
+
         dl = sorted(done_lat)
+        svc_mix = [svc_t[picks[k]] for k in range(n_req)]
         rows.append({"rate_per_s": rate if rate != float("inf") else "all at once", "requests": n_req,
                      "served": {"qps": n_req / wall, "p50_ms": dl[len(dl) // 2],
                                 "p99_ms": dl[min(len(dl) - 1, int(0.99 * len(dl)))],
                                 "max_in_flight": st["max_in_flight"], "kernel_launches": st["kernel_launches"]},
-                     "one_at_a_time": {"qps": n_req / (fin * 1e-3), "p50_ms": lat1[len(lat1) // 2],
-                                       "p99_ms": lat1[min(len(lat1) - 1, int(0.99 * len(lat1)))]}})
+                     "plain_service_tuned_ms": {"mean": statistics.mean(svc_mix),
+                                                "p50": float(np.percentile(svc_mix, 50)),
+                                                "p99": float(np.percentile(svc_mix, 99))},
+                     "one_at_a_time": replay(svc), "one_at_a_time_tuned": replay(svc_t)})
     sys.setswitchinterval(switch)
     info = srv.stats()
     srv.close()
@@ -535,7 +571,10 @@ def serving(eic, torch, stream, rates, seconds_per_rate, max_per_rate):
             "generate_s": gen_s, "groups": info["groups"], "blocks_per_group": info["blocks_per_group"],
             "tuned_gap_shift_per_graph": shifts, "tune_s": tune_s,
             "plain_one_at_a_time_qps": plain_qps, "plain_service_ms_mean": statistics.mean(svc),
-            "rates": rows, "peak_served_qps": best, "speedup_vs_one_at_a_time": best / plain_qps,
+            "plain_tuned_one_at_a_time_qps": plain_t_qps, "plain_tuned_service_ms_mean": statistics.mean(svc_t),
+            "rates": rows, "peak_served_qps": best, "speedup_vs_one_at_a_time": best / plain_t_qps,
+            "speedup_basis": "peak served queries/s vs one-at-a-time plain solves at the same per-graph step width",
+            "speedup_vs_one_at_a_time_default_width": best / plain_qps,
             "latency": "submit to completion seen by the host runtime; one-at-a-time latencies replay the measured "
                        "plain service times of the same requests in arrival order"}
 
@@ -638,40 +677,35 @@ def main():
     achieved = statistics.mean(b / (t * 1e-3) / 1e9 for b, t in zip(b_alg, k_ms))
     peak, peak_kind = peaks()
 
-    # ---- end to end: sources from pinned host memory, distances back to pinned host memory
+    # ---- end to end through the C ABI with host buffers: eic_sssp takes each
+    # source id from the host and writes the distances into page-locked host
+    # memory (its output kernel stores them across the host link); the result
+    # is in host memory when the call returns
     e2e = None
     if not args.no_e2e:
-        src_host = torch.tensor(srcs, dtype=torch.int32).pin_memory()
-        src_dev = torch.empty(q, dtype=torch.int32, device="cuda")
         host_out = [torch.empty(n, dtype=torch.int32).pin_memory() for _ in range(2)]
-        copy_stream = torch.cuda.Stream()  # each query's download overlaps the next query
-        copied = [None] * q
+        for i, s in enumerate(srcs[:2]):  # warm-up; also checks the host copies against the device results
+            eic.sssp(g, s, dist=host_out[i])
+            if not torch.equal(host_out[i], dists[i].cpu()):
+                raise RuntimeError("host-buffer result differs from the device-buffer result")
         torch.cuda.synchronize()
         if world > 1:
             torch.distributed.barrier()
         e_start = torch.cuda.Event(enable_timing=True)
         e_end = torch.cuda.Event(enable_timing=True)
+        t_wall = time.perf_counter()
         e_start.record(stream)
         for _ in range(args.steps):
-            src_dev.copy_(src_host, non_blocking=True)
-            srcs_now = src_dev.cpu().tolist()  # the query API takes host source ids
-            for i, s in enumerate(srcs_now):
-                if copied[i] is not None:  # dists[i] is rewritten only after its last download
-                    stream.wait_event(copied[i])
-                eic.sssp(g, s, dist=dists[i])
-                done = torch.cuda.Event()
-                done.record(stream)
-                copy_stream.wait_event(done)
-                with torch.cuda.stream(copy_stream):
-                    host_out[i & 1].copy_(dists[i], non_blocking=True)
-                    copied[i] = torch.cuda.Event()
-                    copied[i].record(copy_stream)
-        stream.wait_stream(copy_stream)  # the timed region ends after the last download
+            for i, s in enumerate(srcs):
+                eic.sssp(g, s, dist=host_out[i & 1])
         e_end.record(stream)
         torch.cuda.synchronize()
-        e2e_ms = max_over_ranks(e_start.elapsed_time(e_end), world, "cuda")
+        wall_ms = (time.perf_counter() - t_wall) * 1e3
+        e2e_ms = max_over_ranks(max(e_start.elapsed_time(e_end), wall_ms), world, "cuda")
         e2e = {"value": whole_job_gteps(edges_all_ranks, args.steps, e2e_ms), "unit": "GTEPS",
-               "h2d_bytes_per_step": 4 * q, "d2h_bytes_per_step": 4 * n * q}
+               "h2d_bytes_per_step": 4 * q, "d2h_bytes_per_step": 4 * n * q,
+               "how": "eic_sssp per query with a page-locked host output array (host-to-device: the source id "
+                      "passed to the call; device-to-host: n distances written by the output kernel)"}
 
     batched = None
     if not args.no_batched and world == 1:

@@ -183,11 +183,17 @@ int eic_graph_destroy(eic_graph* g);
  * One single-source query by Algorithm 1 (dynamic stepping, Eq. 1-3;
  * traversal optimisation, Function 1/2), exact distances.
  *   source   0 <= source < n.
- *   dist     device array of n uint32, caller-owned; receives lsp(source, v)
- *            or EIC_INF.
- *   parent   device array of n uint32 or NULL; receives the smallest-id u
- *            with dist[u] + w(u, v) == dist[v] (parent[source] = source,
- *            EIC_INF where unreachable).
+ *   dist     array of n uint32, caller-owned; receives lsp(source, v) or
+ *            EIC_INF. Device memory of the graph's GPU, managed memory, or
+ *            page-locked host memory mapped for the device (cudaHostAlloc,
+ *            or cudaHostRegister with a device mapping): the output kernel
+ *            then writes the host array directly across the host link, so
+ *            the result is in host memory when the call returns. Any other
+ *            pointer (pageable host memory, another GPU's memory) is
+ *            rejected with EIC_EINVAL before anything is launched.
+ *   parent   NULL, or an array of n uint32 with the same rules as dist;
+ *            receives the smallest-id u with dist[u] + w(u, v) == dist[v]
+ *            (parent[source] = source, EIC_INF where unreachable).
  *   params   NULL for eic_params_default().
  *   stats    NULL, or a host struct that receives the counters (and the
  *            trace rows when stats->trace is set).
@@ -261,6 +267,10 @@ int eic_sssp_batch(const eic_graph* const* graphs, const uint32_t* sources, uint
  *                   dists hold a complete result afterwards. best (or NULL)
  *                   receives the chosen configuration. Synchronous.
  * eic_batch_info    the current configuration.
+ * eic_batch_gap_shifts  each query's step-width scaling in use (host array
+ *                   of num_queries, in the caller's query order; the tuner
+ *                   chooses it per graph): the value to give eic_sssp in
+ *                   eic_params.gap_shift for the same schedule.
  * eic_batch_destroy frees the batch (NULL accepted); no run may be in flight.
  */
 typedef struct eic_batch eic_batch;
@@ -284,6 +294,7 @@ int eic_batch_run(eic_batch* b, void* stream);
 int eic_batch_wait(eic_batch* b, void* stream, int* statuses);
 int eic_batch_tune(eic_batch* b, void* stream, eic_batch_config* best);
 int eic_batch_info(const eic_batch* b, eic_batch_config* out);
+int eic_batch_gap_shifts(const eic_batch* b, uint32_t* gap_shifts);
 int eic_batch_destroy(eic_batch* b);
 
 /*

@@ -30,7 +30,7 @@ FLAG_NO_PULL = 1
 EXPORTS = ("eic_params_default", "eic_strerror", "eic_version", "eic_graph_create", "eic_graph_info",
            "eic_graph_export", "eic_graph_export_internal", "eic_graph_memory", "eic_graph_destroy", "eic_sssp", "eic_sssp_batch",
            "eic_sssp_noalloc", "eic_batch_create", "eic_batch_run", "eic_batch_wait", "eic_batch_tune",
-           "eic_batch_info", "eic_batch_destroy", "eic_server_create", "eic_server_submit", "eic_server_poll",
+           "eic_batch_info", "eic_batch_gap_shifts", "eic_batch_destroy", "eic_server_create", "eic_server_submit", "eic_server_poll",
            "eic_server_wait", "eic_server_result", "eic_server_release", "eic_server_stats",
            "eic_server_reset_stats", "eic_server_tune", "eic_server_destroy")
 
@@ -138,6 +138,8 @@ def load_library(path: str | None = None):
         L.eic_batch_tune.restype = c_int
         L.eic_batch_info.argtypes = [vp, ctypes.POINTER(BatchConfig)]
         L.eic_batch_info.restype = c_int
+        L.eic_batch_gap_shifts.argtypes = [vp, vp]
+        L.eic_batch_gap_shifts.restype = c_int
         L.eic_batch_destroy.argtypes = [vp]
         L.eic_batch_destroy.restype = c_int
         L.eic_server_create.argtypes = [ctypes.POINTER(vp), u32, ctypes.POINTER(Params), ctypes.POINTER(ServerConfig),
@@ -369,6 +371,12 @@ class Batch:
         c = BatchConfig()
         _check(load_library().eic_batch_info(self._h, ctypes.byref(c)), "eic_batch_info")
         return _config_dict(c)
+
+    def gap_shifts(self) -> list:
+        """Each query's step-width scaling in use (the tuner picks it per graph)."""
+        out = np.zeros(self.n, dtype=np.uint32)
+        _check(load_library().eic_batch_gap_shifts(self._h, out.ctypes.data), "eic_batch_gap_shifts")
+        return out.tolist()
 
     def close(self):
         if getattr(self, "_h", None) and self._h.value and _lib is not None:

@@ -459,7 +459,7 @@ int build(eic_graph* g, const uint32_t* src, const uint32_t* dst, const uint32_t
   }
 
   // 4. both directions in internal ids, stable sort by (row, weight): rows in weight order
-  TRY(galloc(g, &g->adj, E));
+  TRY(galloc(g, &g->adj, E + 2));  // two spare entries: a 16-byte pair load starting at the last entry stays inside
   if (E > 0) {
     uint64_t *ek0, *ek1;
     uint32_t *ev0, *ev1;

@@ -805,55 +805,152 @@ __device__ void task_phase(const KArgs& A, const RoundCtx& R, uint32_t ntasks, S
   stage_flush(T, R, A.tasks);
 }
 
+// The first candidate index with the largest positive profit over the block
+// (ties: the smaller index), or 0xFFFFFFFF when no profit is positive.
+__device__ __forceinline__ uint32_t block_argmax(S3Scr& S, double best, uint32_t bk) {
+  const uint32_t t = threadIdx.x, nt = blockDim.x;
+  for (int o = 16; o > 0; o >>= 1) {
+    double ob = __shfl_down_sync(EIC_FULL_MASK, best, o);
+    uint32_t ok = __shfl_down_sync(EIC_FULL_MASK, bk, o);
+    if (ob > best || (ob == best && ok < bk)) {
+      best = ob;
+      bk = ok;
+    }
+  }
+  __syncthreads();
+  if ((t & 31) == 0) {
+    S.bp[t >> 5] = best;
+    S.bk[t >> 5] = bk;
+  }
+  __syncthreads();
+  if (t < 32) {
+    best = t < (nt >> 5) ? S.bp[t] : 0.0;
+    bk = t < (nt >> 5) ? S.bk[t] : 0xFFFFFFFFu;
+    for (int o = 16; o > 0; o >>= 1) {
+      double ob = __shfl_down_sync(EIC_FULL_MASK, best, o);
+      uint32_t ok = __shfl_down_sync(EIC_FULL_MASK, bk, o);
+      if (ob > best || (ob == best && ok < bk)) {
+        best = ob;
+        bk = ok;
+      }
+    }
+    if (t == 0) S.bk[0] = bk;
+  }
+  __syncthreads();
+  const uint32_t k = S.bk[0];
+  __syncthreads();
+  return k;
+}
+
+// Function 2 for weights of 2^20 and above (one block), with D(x') summed
+// exactly from the settled list: over the entries of the steps
+// j (from j0 to step) that end above wl, the vertex at distance d >= wl adds
+// its degree to bin 1 + k_d, k_d the last candidate k with x_k <= d (-1 if
+// none); after a suffix sum, D(x_k) is bin 1 + k for x_k >= wl and bin 0 for a
+// candidate clamped to wl. The bins are in shared memory, or in the ring
+// (2^20 slots, unused for such weights) when ST_NUM is large.
+__device__ __forceinline__ int64_t block_st_exact(const KArgs& A, S3Scr& S, int64_t ub, uint64_t sumd_ub,
+                                                  int64_t gap_lb, int64_t gap_ub_raw, int64_t y, int64_t st0,
+                                                  int64_t st1, uint32_t j0, uint32_t step, uint32_t send) {
+  __shared__ uint32_t s_beg;
+  const uint32_t t = threadIdx.x, nt = blockDim.x;
+  const int64_t maxw = A.G.maxw;
+  if (sumd_ub >= A.G.m || gap_lb == maxw) return ub;
+  if (gap_ub_raw == maxw) return ub - maxw;
+  const int64_t wl = ub - maxw > 0 ? ub - maxw : 0;
+  const uint64_t nbins = (uint64_t)A.st_num + 2;
+  const bool sh = nbins <= kStBins;
+  unsigned long long* bins = sh ? S.bins : A.ring;
+  for (uint64_t q = t; q < nbins; q += nt) bins[q] = 0ull;
+  if (t == 0) {
+    uint32_t j = j0;
+    while (j <= step && __ldcg(&A.step_ub[j]) <= wl) ++j;
+    s_beg = j <= step ? __ldcg(&A.step_off[j]) : send;
+  }
+  __syncthreads();
+  const uint64_t span = (uint64_t)(st1 - st0);
+  for (uint32_t i = s_beg + t; i < send; i += nt) {
+    const int64_t d = ld_list(&A.sd[i]);
+    if (d < wl) continue;
+    const uint2 rr = ld_list2(&A.srow[i]);
+    uint64_t cnt;  // how many x_k are <= d: the k with k (st1 - st0) < (d - st0 + 1) ST_NUM
+    if (d < st0)
+      cnt = 0;
+    else if (span == 0)
+      cnt = nbins - 1;
+    else
+      cnt = min(((uint64_t)(d - st0 + 1) * A.st_num + span - 1) / span, nbins - 1);
+    atomicAdd(&bins[cnt], (unsigned long long)(rr.y - rr.x));
+  }
+  __syncthreads();
+  // suffix sums: chunk totals, a scan over the chunks, then within the chunks
+  const uint64_t cs = (nbins + nt - 1) / nt;
+  const uint64_t q0 = t * cs, q1 = min(nbins, q0 + cs);
+  unsigned long long mine = 0;
+  for (uint64_t q = q0; q < q1; ++q) mine += sh ? bins[q] : __ldcg(&bins[q]);
+  S.part[t] = mine;
+  __syncthreads();
+  for (uint32_t o = 1; o < nt; o <<= 1) {
+    unsigned long long v = t + o < nt ? S.part[t + o] : 0;
+    __syncthreads();
+    S.part[t] += v;
+    __syncthreads();
+  }
+  unsigned long long acc = t + 1 < nt ? S.part[t + 1] : 0;
+  for (uint64_t q = q1; q > q0; --q) {
+    acc += sh ? bins[q - 1] : __ldcg(&bins[q - 1]);
+    if (sh)
+      bins[q - 1] = acc;
+    else
+      __stcg(&bins[q - 1], acc);
+  }
+  __syncthreads();
+  double best = 0.0;
+  uint32_t bk = 0xFFFFFFFFu;
+  for (uint32_t k = t; k <= A.st_num; k += nt) {
+    const int64_t x = st0 + (int64_t)(((uint64_t)k * span) / A.st_num);
+    if (x >= ub) continue;
+    const uint64_t q = x >= wl ? (uint64_t)k + 1 : 0;
+    const unsigned long long dsum = sh ? bins[q] : __ldcg(&bins[q]);
+    const double p = dev_profit(x, ub, y, dsum, sumd_ub, A.G.maxw, A.G.two_m);
+    if (p > best) {
+      best = p;
+      bk = k;
+    }
+  }
+  const uint32_t k = block_argmax(S, best, bk);
+  if (k == 0xFFFFFFFFu) return ub;
+  return st0 + (int64_t)(((uint64_t)k * span) / A.st_num);
+}
+
+// The same out of line, for the batch and serving kernels: inlined there it
+// costs their query loop registers (and their speed), while the single-query
+// kernel is not affected either way.
+__device__ __noinline__ int64_t block_st_exact_call(const KArgs& A, S3Scr& S, int64_t ub, uint64_t sumd_ub,
+                                                    int64_t gap_lb, int64_t gap_ub_raw, int64_t y, int64_t st0,
+                                                    int64_t st1, uint32_t j0, uint32_t step, uint32_t send) {
+  return block_st_exact(A, S, ub, sumd_ub, gap_lb, gap_ub_raw, y, st0, st1, j0, step, send);
+}
+
 // Function 2 for the boundary <lb, ub> -> next pair <ub, ub + gap(ub)>, run by
 // one whole block. Candidates x_k = st0 + floor(k (st1 - st0) / ST_NUM) < ub;
 // D(x') = sumD(x') - sumD(ub), the degree sum of the settled vertices with
-// x' <= dist < ub, where x' >= wl = max(ub - maxW, 0). While maxW < 2^20 it is
-// read from the ring of settled degree sums (one slot per distance). For wider
-// weights it is summed exactly from the settled list entries [sbeg, send)
-// (the steps that end above wl): a vertex at distance d >= wl adds its degree
-// to bin 1 + k_d, k_d the last k with x_k <= d (-1 if none), so that D(x_k) is
-// the sum of the bins from 1 + k, and D(wl) of all of them.
+// x' <= dist < ub, x' = max(x, ub - maxW), read from the ring of settled
+// degree sums (one slot per distance: maxW < 2^20; wider weights go through
+// block_st_exact).
 __device__ int64_t block_compute_st(const KArgs& A, S3Scr& S, int64_t ub, uint64_t sumd_ub, int64_t gap_lb,
-                                    int64_t gap_ub_raw, int64_t y, int64_t st0, int64_t st1, uint32_t sbeg,
-                                    uint32_t send) {
+                                    int64_t gap_ub_raw, int64_t y, int64_t st0, int64_t st1) {
   const int64_t maxw = A.G.maxw;
   if (sumd_ub >= A.G.m || gap_lb == maxw) return ub;
   if (gap_ub_raw == maxw) return ub - maxw;
   const uint32_t t = threadIdx.x, nt = blockDim.x;
   const int64_t wl = ub - maxw > 0 ? ub - maxw : 0;
-  const bool by_ring = A.ring_shift == 0;
-  const uint64_t nbins = (uint64_t)A.st_num + 2;
-  const bool sh_bins = nbins <= kStBins;
-  unsigned long long* bins = sh_bins ? S.bins : A.ring;  // the ring (2^20 slots) is unused for wide weights
-  if (!by_ring) {
-    for (uint64_t q = t; q < nbins; q += nt) bins[q] = 0ull;
-    __syncthreads();
-    const uint64_t span = (uint64_t)(st1 - st0);
-    for (uint32_t i = sbeg + t; i < send; i += nt) {
-      const int64_t d = ld_list(&A.sd[i]);
-      if (d < wl) continue;
-      const uint2 rr = ld_list2(&A.srow[i]);
-      uint64_t cnt;  // how many x_k are <= d: the k with k (st1 - st0) < (d - st0 + 1) ST_NUM
-      if (d < st0)
-        cnt = 0;
-      else if (span == 0)
-        cnt = nbins - 1;
-      else
-        cnt = min(((uint64_t)(d - st0 + 1) * A.st_num + span - 1) / span, nbins - 1);
-      atomicAdd(&bins[cnt], (unsigned long long)(rr.y - rr.x));
-    }
-    __syncthreads();
-  }
-  const uint64_t sl = by_ring ? (uint64_t)wl : 0, su = by_ring ? (uint64_t)(ub - 1) : nbins - 1;
-  auto slot = [&](uint64_t q) -> unsigned long long {
-    if (by_ring) return __ldcg(&A.ring[q & A.ring_mask]);
-    return sh_bins ? bins[q] : __ldcg(&bins[q]);
-  };
-  const uint64_t L = su - sl + 1;  // slots covering [wl, ub), or the bins
+  const uint32_t sh = A.ring_shift;
+  const uint64_t sl = (uint64_t)wl >> sh, su = (uint64_t)(ub - 1) >> sh;
+  const uint64_t L = su - sl + 1;  // ring slots covering [wl, ub)
   const uint64_t cs = (L + nt - 1) / nt;
   unsigned long long mine = 0;
-  for (uint64_t q = sl + t * cs; q < sl + (t + 1) * cs && q <= su; ++q) mine += slot(q);
+  for (uint64_t q = sl + t * cs; q < sl + (t + 1) * cs && q <= su; ++q) mine += __ldcg(&A.ring[q & A.ring_mask]);
   S.part[t] = mine;
   __syncthreads();
   for (uint32_t o = 1; o < nt; o <<= 1) {  // suffix sums over chunks
@@ -872,10 +969,10 @@ __device__ int64_t block_compute_st(const KArgs& A, S3Scr& S, int64_t ub, uint64
       const int64_t xp = st0 + (int64_t)(((uint64_t)(k - 1) * (uint64_t)(st1 - st0)) / A.st_num);
       if ((xp > ub - maxw ? xp : ub - maxw) == xc) continue;
     }
-    const uint64_t q0 = by_ring ? (uint64_t)xc : (x >= wl ? (uint64_t)k + 1 : 0);
+    const uint64_t q0 = (uint64_t)xc >> sh;
     const uint64_t c = (q0 - sl) / cs;
     unsigned long long dsum = c + 1 < nt ? S.part[c + 1] : 0;
-    for (uint64_t q = q0; q < sl + (c + 1) * cs && q <= su; ++q) dsum += slot(q);
+    for (uint64_t q = q0; q < sl + (c + 1) * cs && q <= su; ++q) dsum += __ldcg(&A.ring[q & A.ring_mask]);
     const double p = dev_profit(x, ub, y, dsum, sumd_ub, A.G.maxw, A.G.two_m);
     if (p > best) {
       best = p;
@@ -920,6 +1017,7 @@ __device__ int64_t block_compute_st(const KArgs& A, S3Scr& S, int64_t ub, uint64
 // statistics pass: sumD(ub), highD(ub), gap(ub) (Eq. 1-3), termination
 // (Algorithm 1), computeST (Function 2) and the push/pull sets of the next
 // step's Function 1. Publishes the new control values before the grid barrier.
+template <bool kExactInline>
 __device__ void step_boundary(const KArgs& A, PhaseScr& P, BState& B, const Local& L, uint32_t rounds_in_step) {
   Ctl* c = A.ctl;
   __shared__ int64_t sh_i[8];
@@ -994,19 +1092,17 @@ __device__ void step_boundary(const KArgs& A, PhaseScr& P, BState& B, const Loca
     if (B.st1 < 0 && sumd_ub <= G.m) B.st1 = ub;
     sh_i[1] = gap_raw;
     sh_i[2] = gap_raw << A.gap_shift;
-    // the settled-list entries of the steps ending above ub - maxW (from the first such step on)
-    const int64_t wl = ub - (int64_t)G.maxw > 0 ? ub - (int64_t)G.maxw : 0;
-    uint32_t j = B.j0;
-    while (j <= k && __ldcg(&A.step_ub[j]) <= wl) ++j;
-    sh_u[2] = j <= k ? __ldcg(&A.step_off[j]) : sh_u[1];
   }
   __syncthreads();
   const int64_t gap_raw = sh_i[1], width = sh_i[2];
   const int64_t nlb = ub, nub = ub + width;
   const int64_t nst = (A.flags & EIC_FLAG_NO_PULL) ? nlb
-                                                    : block_compute_st(A, P.s3, ub, sumd_ub, B.gap_lb, gap_raw, nub,
-                                                                       B.st0, B.st1, (uint32_t)sh_u[2],
-                                                                       (uint32_t)sh_u[1]);
+                      : A.ring_shift == 0
+                          ? block_compute_st(A, P.s3, ub, sumd_ub, B.gap_lb, gap_raw, nub, B.st0, B.st1)
+                          : kExactInline ? block_st_exact(A, P.s3, ub, sumd_ub, B.gap_lb, gap_raw, nub, B.st0, B.st1,
+                                                          B.j0, k, (uint32_t)sh_u[1])
+                                         : block_st_exact_call(A, P.s3, ub, sumd_ub, B.gap_lb, gap_raw, nub, B.st0,
+                                                               B.st1, B.j0, k, (uint32_t)sh_u[1]);
   if (A.ring_shift == 0) {  // zero the ring slots the next statistics pass fills: [max(nlb, nub - maxW), nub)
     const int64_t zl = nub - (int64_t)G.maxw > nlb ? nub - (int64_t)G.maxw : nlb;
     const uint64_t ql = (uint64_t)zl >> A.ring_shift, qu = (uint64_t)(nub - 1) >> A.ring_shift;
@@ -1398,7 +1494,7 @@ __device__ void run_query(const KArgs& A, QueryShared& Q, uint32_t& gen) {
           tl_mark(A, 4, L.rid);
         }
         __syncthreads();
-        if (sh_last) step_boundary(A, P, B, L, rin);
+        if (sh_last) step_boundary<(kRelaxIlp >= 2)>(A, P, B, L, rin);  // (the single-query shape inlines)
         if (threadIdx.x == 0) tl_mark(A, 5, L.rid);
       }
     }
@@ -2003,16 +2099,45 @@ int enqueue_query(eic_graph* g, uint32_t s, uint32_t* dist, uint32_t* parent, co
   return EIC_OK;
 }
 
-int trivial_query(eic_graph* g, uint32_t s, uint32_t* dist, uint32_t* parent, cudaStream_t st) {
-  const uint64_t n = g->dg.n;
-  EIC_CUDA_TRY(cudaMemsetAsync(dist, 0xFF, n * 4, st));
-  EIC_CUDA_TRY(cudaMemsetAsync(dist + s, 0, 4, st));
-  if (parent) {
-    EIC_CUDA_TRY(cudaMemsetAsync(parent, 0xFF, n * 4, st));
-    EIC_CUDA_TRY(cudaMemcpyAsync(parent + s, &s, 4, cudaMemcpyHostToDevice, st));
+// A graph without edges: only the source is reachable (its own parent).
+__global__ void k_trivial(uint32_t n, uint32_t s, uint32_t* dist, uint32_t* parent) {
+  for (uint64_t u = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; u < n; u += (uint64_t)gridDim.x * blockDim.x) {
+    dist[u] = u == s ? 0u : EIC_INF;
+    if (parent) parent[u] = u == s ? s : EIC_INF;
   }
+}
+
+int trivial_query(eic_graph* g, uint32_t s, uint32_t* dist, uint32_t* parent, cudaStream_t st) {
+  k_trivial<<<256, 256, 0, st>>>(g->dg.n, s, dist, parent);
+  EIC_CUDA_TRY(cudaGetLastError());
   EIC_CUDA_TRY(cudaStreamSynchronize(st));
   return EIC_OK;
+}
+
+// The device's address of an output array of the graph's GPU: its device
+// memory, managed memory, or page-locked host memory mapped for the device
+// (written across the host link). Anything else is rejected before launch.
+int output_view(int dev, uint32_t* p, uint32_t** out) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return EIC_EINVAL;
+  }
+  switch (a.type) {
+    case cudaMemoryTypeDevice:
+      if (a.device != dev) return EIC_EINVAL;
+      *out = p;
+      return EIC_OK;
+    case cudaMemoryTypeManaged:
+      *out = p;
+      return EIC_OK;
+    case cudaMemoryTypeHost:
+      if (!a.devicePointer) return EIC_EINVAL;
+      *out = (uint32_t*)a.devicePointer;
+      return EIC_OK;
+    default:
+      return EIC_EINVAL;
+  }
 }
 
 }  // namespace
@@ -2100,6 +2225,8 @@ int eic_sssp(const eic_graph* gc, uint32_t source, uint32_t* dist, uint32_t* par
   DeviceGuard dg(g->device);
   if (!dg.ok) return EIC_ECUDA;
   cudaStream_t st = (cudaStream_t)stream;
+  if ((rc = output_view(g->device, dist, &dist)) || (parent && (rc = output_view(g->device, parent, &parent))))
+    return rc;
   eic_step* trace = stats ? stats->trace : nullptr;
   const uint64_t trace_cap = stats ? stats->trace_cap : 0;
   uint64_t* tl = stats ? stats->timeline : nullptr;
@@ -2645,6 +2772,13 @@ int eic_batch_info(const eic_batch* b, eic_batch_config* out) {
   out->queries = b->nq;
   out->scratch_bytes = (uint64_t)b->pool->count * b->pool->slot_bytes;
   out->tuned_ms = b->tuned_ms;
+  return EIC_OK;
+}
+
+int eic_batch_gap_shifts(const eic_batch* b, uint32_t* gap_shifts) {
+  if (!b || !gap_shifts) return EIC_EINVAL;
+  for (uint32_t i = 0; i < b->nq; ++i) gap_shifts[i] = b->p.gap_shift;  // graphs without edges keep the batch's
+  for (size_t k = 0; k < b->hq.size(); ++k) gap_shifts[b->order[k]] = b->hq[k].gap_shift;
   return EIC_OK;
 }
 

@@ -82,7 +82,28 @@ def test_batch_plan_replays_cuda_graph_and_tunes(mixed):
     b.run()
     assert (b.wait() == 0).all()
     _check(dists, want)
+    # each query's tuned step width, and the plain path at that width gives the same distances
+    shifts = b.gap_shifts()
+    assert len(shifts) == len(srcs) and max(shifts) <= 8 and max(shifts) == cfg["gap_shift"]
+    for g, s, sh, w in zip(graphs, srcs, shifts, want):
+        d, rc, _ = eic.sssp(g, s, params=eic.default_params(gap_shift=sh))
+        assert rc == 0 and np.array_equal(eic.to_host_u32(d), w)
     b.close()
+
+
+def test_batch_wide_weights_exact():
+    """Weights of 2^20 and above (Function 2's exact sums, out of line in the
+    batch kernel): every query equals Dijkstra for several group counts."""
+    wl = G.kron(12, seed=92, weights=f"uniform:{1 << 24}", nsources=6)
+    g = eic.Graph(wl.n, wl.src, wl.dst, wl.w)
+    og = O.Graph(wl.n, wl.src, wl.dst, wl.w)
+    srcs = [int(s) for s in wl.sources]
+    want = [og.dijkstra(s)[0] for s in srcs]
+    for groups in (1, 3):
+        dists = [eic.new_dist(g.n) for _ in srcs]
+        st = eic.sssp_batch([g] * len(srcs), srcs, dists, params=eic.default_params(batch_groups=groups))
+        assert (st == 0).all(), st
+        _check(dists, want)
 
 
 def test_batch_trivial_isolated_and_repeated_sources():

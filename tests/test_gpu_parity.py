@@ -156,6 +156,33 @@ def test_parent_output():
         assert np.array_equal(eic.to_host_u32(par), og.parent(int(s), d))
 
 
+def test_host_output_arrays():
+    """dist and parent in page-locked host memory are written directly by the
+    query; pageable host memory is rejected before any launch."""
+    wl = G.kron(12, seed=34, nsources=2)
+    g, og = _pair(wl)
+    for s in wl.sources:
+        s = int(s)
+        d = torch.empty(wl.n, dtype=torch.int32).pin_memory()
+        p = torch.empty(wl.n, dtype=torch.int32).pin_memory()
+        d.fill_(7)
+        _, rc, _ = eic.sssp(g, s, dist=d, parent=p)
+        want, _ = og.dijkstra(s)
+        assert rc == 0 and np.array_equal(d.numpy().view(np.uint32), want)
+        assert np.array_equal(p.numpy().view(np.uint32), og.parent(s, want))
+    pageable = torch.empty(wl.n, dtype=torch.int32)
+    _, rc, _ = eic.sssp(g, int(wl.sources[0]), dist=pageable, raise_on_error=False)
+    assert rc == binding.EINVAL
+    dev = eic.new_dist(wl.n)
+    _, rc, _ = eic.sssp(g, int(wl.sources[0]), dist=dev, parent=pageable, raise_on_error=False)
+    assert rc == binding.EINVAL
+    # a graph without edges, host output
+    g0 = eic.Graph(5, np.zeros(0, np.uint32), np.zeros(0, np.uint32), np.zeros(0, np.uint32))
+    d = torch.empty(5, dtype=torch.int32).pin_memory()
+    _, rc, _ = eic.sssp(g0, 3, dist=d)
+    assert rc == 0 and d.numpy().view(np.uint32).tolist() == [eic.EIC_INF] * 3 + [0, eic.EIC_INF]
+
+
 def test_no_pull_and_step_scaling_stay_exact():
     wl = G.kron(14, seed=31, nsources=2)
     g, og = _pair(wl)
