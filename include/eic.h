@@ -312,8 +312,14 @@ int eic_batch_destroy(eic_batch* b);
  * while there is work: after config.idle_us without a request, once no
  * request runs, a block group registers as idle, and when every group is
  * registered they leave together; the runtime relaunches the kernel when
- * requests arrive again. Scratch: one slot per group sized for the largest
- * resident graph (as a batch's).
+ * requests arrive again. The width of a launch follows the backlog: with at
+ * most 4 (8, 16) waiting requests it runs 4 (8, 16) groups that share the
+ * co-resident blocks, else config.groups groups; a launch with fewer groups
+ * ends (each group after its current request) once twice its group count of
+ * admitted requests wait, and the runtime relaunches wider. A lone request
+ * thus runs on a quarter of the GPU, not on one small group. Scratch: one
+ * slot per group (config.groups slots) sized for the largest resident graph
+ * (as a batch's).
  *
  * eic_server_create   graphs (host array of num_graphs, all on one device)
  *                     stay owned by the caller and must outlive the server;

@@ -119,7 +119,9 @@ struct eic_server {
   std::vector<BatchQuery> hq;  // the resident graphs' table (host copy of d_graphs)
   BatchQuery* d_graphs = nullptr;
   eic_params p{};
-  uint32_t groups = 0, nb = 0, block = 0, cap = 0;
+  uint32_t groups = 0, nb = 0, block = 0, cap = 0;  // groups (slots) at most, blocks per group at that count
+  uint32_t gmax = 0;                                 // co-resident blocks of the serving kernel
+  uint32_t launch_groups = 0;                        // groups of the running (or last) launch
   uint64_t idle_ns = 0;
   SlotPool pool;
   Arena arena;
@@ -143,7 +145,17 @@ struct eic_server {
   uint64_t next_ticket = 0, seq = 0, completed = 0, max_inflight = 0, submitted = 0;
   std::vector<double> lat_ms;                  // completed requests' latencies
 
-  ServeArgs args() const {
+  // The launch's group count for a backlog of waiting requests: a few wide
+  // groups while the backlog is short (a lone request runs on a quarter of
+  // the GPU, not on one of many small groups), more and narrower groups as it
+  // grows, up to every slot the server has.
+  uint32_t launch_shape(uint64_t backlog) const {
+    for (uint32_t g : {4u, 8u, 16u})
+      if (g < groups && backlog <= g) return g;
+    return groups;
+  }
+
+  ServeArgs args(uint32_t g) const {
     ServeArgs a;
     a.ring = dring;
     a.req = serve_requests(dring);
@@ -153,7 +165,7 @@ struct eic_server {
     a.slot = pool.d_slots;
     a.num_graphs = (uint32_t)graphs.size();
     a.cap = cap;
-    a.nb = nb;
+    a.nb = g == groups ? nb : gmax / g;
     a.alpha = p.alpha;
     a.beta = p.beta;
     a.st_num = p.st_num;
@@ -163,9 +175,10 @@ struct eic_server {
     a.step_cap = kServeStepCap;
     const uint32_t sl = p.max_spin_log2 > kServeSpinLog2 ? p.max_spin_log2 : kServeSpinLog2;
     a.max_spin = 1ull << sl;
-    a.groups = groups;
+    a.groups = g;
     a.idle_ns = idle_ns;
     a.poll_ns = kPollUs * 1000ull;
+    a.widen_at = g < groups ? 2ull * g : 0ull;
     return a;
   }
 
@@ -222,7 +235,8 @@ struct eic_server {
       }
     }
     if (!running && !admitted.empty() && launch_error == EIC_OK) {
-      int rc = eic_serve_launch(args(), groups, block, kstream);
+      launch_groups = launch_shape(admitted.size());
+      int rc = eic_serve_launch(args(launch_groups), launch_groups, block, kstream);
       if (rc == EIC_OK && cudaEventRecord(kdone, kstream) != cudaSuccess) rc = EIC_ECUDA;
       if (rc != EIC_OK) {
         (void)cudaGetLastError();
@@ -378,6 +392,7 @@ int eic_server_create(const eic_graph* const* graphs, uint32_t num_graphs, const
     }
     s->groups = groups;
     s->nb = gmax / groups;
+    s->gmax = gmax;
   }
   if ((rc = s->pool.ensure(caps, s->groups))) goto fail;
   if ((rc = s->arena.init(cfg.output_bytes ? cfg.output_bytes : 64ull * max_n * 4))) goto fail;

@@ -53,6 +53,8 @@ struct ServeArgs {
                                   // no group runs one; all leave together once all are registered
   uint64_t poll_ns;               // longest single wait of a group's first thread before the group
                                   // passes its barrier and waits again (keeps barrier waits short)
+  uint64_t widen_at;              // 0, or: once this many admitted requests wait unclaimed, every group
+                                  // leaves after its current request (the host relaunches more groups)
 };
 
 // Launch the serving kernel: `groups` groups of args.nb blocks of `block`

@@ -1800,9 +1800,11 @@ constexpr unsigned long long kRetry = ~0ull - 1;      // nothing yet: the group 
 // and waits again, so no barrier wait comes near its bound). After idle_ns
 // without work, once no group runs a request, a group registers as idle; when
 // every group is registered they all leave together (the host relaunches the
-// kernel when work arrives). They also leave when the host sets stop. A group
-// stops at its first failing request (whose completion carries the error) and
-// counts as idle from then on.
+// kernel when work arrives). They also leave when the host sets stop, and,
+// in a launch with fewer groups than the server has, once widen_at admitted
+// requests wait unclaimed (each after its current request; the host then
+// relaunches with more groups). A group stops at its first failing request
+// (whose completion carries the error) and counts as idle from then on.
 __global__ void __launch_bounds__(kMaxBlock, 2) k_eic_serve(ServeArgs P) {
   __shared__ QueryShared Q;
   __shared__ KArgs sA;
@@ -1830,6 +1832,11 @@ __global__ void __launch_bounds__(kMaxBlock, 2) k_eic_serve(ServeArgs P) {
         }
         const unsigned long long head = ld_acquire_sys_u64(&P.ring->head);
         const unsigned long long cur = atomicAdd(claim, 0ull);
+        if (P.widen_at && cur < head && head - cur >= P.widen_at) {  // a backlog: make room for more groups
+          atomicExch(leave, 1ull);
+          got = kNoTicket;
+          break;
+        }
         if (cur < head) {
           if (atomicCAS(claim, cur, cur + 1) == cur) {
             got = cur;
