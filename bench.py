@@ -403,19 +403,21 @@ def batched_mixed(eic, torch, stream, runs):
 
 def stress(eic, torch, stream, nsources):
     """The stress workloads, on the plain path: the 4096^2 road-like grid
-    (weights [1,4095]) with the default step width and with the exact 16x
-    scaling the autotuners pick for grids, and Kron 25 with log-normal
-    weights. GTEPS = edges in the source's component / query time."""
+    (weights [1,4095]) with the default step width (fused rounds, and for
+    comparison without them) and with the exact 16x scaling the autotuners
+    pick for grids, and Kron 25 with log-normal weights. GTEPS = edges in the
+    source's component / query time."""
     import numpy as np
     from paper_2506_19349_gb300 import graphgen
 
     cases = (
         ("road_4096", "4096^2 grid, 4-neighbour, 10% of edges deleted, 2% diagonal shortcuts, weights uniform "
          "[1,4095], sources from the largest component",
-         lambda: graphgen.road(4096, seed=3, wmax=4095, nsources=nsources), (0, 4)),
+         lambda: graphgen.road(4096, seed=3, wmax=4095, nsources=nsources),
+         (("gap_shift_0", {}), ("gap_shift_0_no_fuse", {"flags": eic.FLAG_NO_FUSE}), ("gap_shift_4", {"gap_shift": 4}))),
         ("kron25_lognormal", "kron25 topology, weights clamp(llround(exp(3 + 1.5 Z)), 1, 65535), sources uniform "
          "over non-isolated vertices", lambda: graphgen.kron(25, seed=2, weights="lognormal", nsources=nsources),
-         (0,)),
+         (("gap_shift_0", {}),)),
     )
     out = {}
     for name, desc, make, shifts in cases:
@@ -428,8 +430,8 @@ def stress(eic, torch, stream, nsources):
         deg = _degrees(eic, g, torch)
         d = eic.new_dist(g.n)
         res = {"workload": desc, "n": g.n, "m": g.m, "sources": len(srcs), "generate_s": gen_s}
-        for sh in shifts:
-            p = eic.default_params(gap_shift=sh)
+        for label, kw in shifts:
+            p = eic.default_params(**kw)
             eic.sssp(g, srcs[0], dist=d, params=p)  # warm-up
             ms, mc, steps, rounds = [], [], [], []
             for s in srcs:
@@ -443,7 +445,7 @@ def stress(eic, torch, stream, nsources):
                 mc.append(_m_c(deg, d))
                 steps.append(info["steps"])
                 rounds.append(info["rounds"])
-            res[f"gap_shift_{sh}"] = {"value": sum(mc) / (sum(ms) * 1e-3) / 1e9, "unit": "GTEPS",
+            res[label] = {"value": sum(mc) / (sum(ms) * 1e-3) / 1e9, "unit": "GTEPS",
                                       "p50_ms": float(np.percentile(ms, 50)), "p99_ms": float(np.percentile(ms, 99)),
                                       "steps_mean": statistics.mean(steps), "rounds_mean": statistics.mean(rounds)}
         out[name] = res

@@ -75,6 +75,7 @@ typedef struct {
 } eic_params;
 
 #define EIC_FLAG_NO_PULL 1u /* force st = lb (disable traversal optimisation; still exact) */
+#define EIC_FLAG_NO_FUSE 2u /* no fused rounds (bucket fusion): every round of a step is a grid-wide round */
 
 /* Per-step trace row: the thresholds a step ran with and the statistics of
  * Section 3 that produced them. */

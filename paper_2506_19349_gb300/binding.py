@@ -25,6 +25,7 @@ NOALLOC_MAX_WEIGHT = 65535
 NOALLOC_MAX_DEGREES = 4096
 NOALLOC_MAX_STEPS = 1 << 14
 FLAG_NO_PULL = 1
+FLAG_NO_FUSE = 2
 
 # Every name declared in include/eic.h.
 EXPORTS = ("eic_params_default", "eic_strerror", "eic_version", "eic_graph_create", "eic_graph_info",

@@ -108,7 +108,8 @@ struct Workspace {
   uint32_t ring_bits = 0, ring_shift = 0;
   uint32_t task_cap = 0, step_cap = 0;
   uint64_t bytes = 0;
-  int grid = 0, block = 0;  // cached cooperative launch shape
+  int grid = 0, block = 0;  // cached cooperative launch shape of k_eic
+  int grid_fused = 0, block_fused = 0;  // and of k_eic_fused
 };
 
 struct eic_graph {

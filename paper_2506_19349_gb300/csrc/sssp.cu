@@ -932,6 +932,118 @@ __device__ __noinline__ int64_t block_st_exact_call(const KArgs& A, S3Scr& S, in
   return block_st_exact(A, S, ub, sumd_ub, gap_lb, gap_ub_raw, y, st0, st1, j0, step, send);
 }
 
+// A fused round: the FUSED local iterations of Section 4.1 (bucket fusion),
+// for graphs in which no window is longer than heavy_min (every degree <=
+// heavy_min, so there are no grid tasks), in the rounds after a step's first.
+// Each warp takes up to 32 of the round's frontier vertices and relaxes their
+// windows; every vertex it improves goes into the warp's local queue (shared
+// memory, kWarpStage entries) and is relaxed by the same warp in its next
+// wave, with the distance it has then, until the local queue is empty. The
+// warps advance independently, with no grid barrier between waves: the round
+// replaces the step's remaining rounds. A vertex improved by two warps is
+// relaxed by both, and the smaller distance wins (within a step any order of
+// the relaxations is exact). What a full local queue cannot take goes to the
+// next round's queue through the round's SAP bitmap, as in a plain round.
+// A wave is one chain of dependent loads (the vertex record, its row, the
+// neighbours' distances, the atomicMin) where a plain round adds a grid
+// barrier and the next round's item fetch.
+__device__ void fused_round(const KArgs& A, const RoundCtx& R, RoundScr& S, Stage& T, uint32_t nitems,
+                            const uint32_t* qin, Counters& C) {
+  const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
+  const uint32_t gwarp = qblock(A) * (blockDim.x >> 5) + warp;
+  WarpScr& W = S.w[warp];
+  uint32_t* lq = T.wq[warp];  // the local queue: a ring of kWarpStage vertex ids
+  uint32_t lh = 0, lt = 0;    // its head and tail (warp-uniform)
+  WarpList Fw = {T.wf[warp], 0u, R.first_cnt, R.first_list};
+  const uint32_t i0 = gwarp * 32;
+  if (i0 < nitems) {
+    if (i0 + lane < nitems) lq[lane] = ld_list(&qin[i0 + lane]);
+    lt = min(32u, nitems - i0);
+  }
+  __syncwarp();
+  while (lh != lt) {
+    const uint32_t k = min(32u, lt - lh);
+    const bool has = lane < k;
+    const uint32_t u = has ? lq[(lh + lane) & (kWarpStage - 1)] : 0u;
+    __syncwarp();
+    lh += k;
+    uint32_t d = EIC_INF, rb = 0, re = 0, len = 0;
+    if (has) {
+      d = __ldcg(&A.dist[u]);
+      rb = __ldg(&A.G.row[u]);
+      re = __ldg(&A.G.row[u + 1]);
+    }
+    // d >= lb: the window is the row's prefix with weight < ub - d; rows are
+    // short, so the whole row is read and filtered (a search only for rows
+    // that keep a cursor)
+    if (has && d != EIC_INF && !(d > 0 && re - rb == 1)) {  // Paths excludes leaves (Algorithm 1)
+      C.frontier += 1;
+      const int64_t hi = R.ub_eff - (int64_t)d;
+      if (hi > 0) {
+        len = re - rb;
+        if (re - rb > kCursorMin) {
+          const uint32_t e = gallop_w(A.G.adj, rb, re, hi);
+          __stcg(&A.cursor[u], e - rb);
+          len = e - rb;
+        }
+      }
+    }
+    const uint32_t incl = warp_incl_scan(len);
+    const uint32_t total = __shfl_sync(EIC_FULL_MASK, incl, 31);
+    W.beg[lane] = rb;
+    W.excl[lane] = incl - len;
+    W.val[lane] = d;
+    __syncwarp();
+    for (uint32_t g0 = 0; g0 < total; g0 += 32) {
+      const uint32_t g = g0 + lane;
+      bool ok = false, first = false;
+      uint32_t v = 0;
+      if (g < total) {
+        uint32_t lo = 0, hi = 31;
+        while (lo < hi) {  // the last lane whose window starts at or before g
+          const uint32_t mid = (lo + hi + 1) >> 1;
+          if (W.excl[mid] <= g)
+            lo = mid;
+          else
+            hi = mid - 1;
+        }
+        const uint2 ent = ld_stream(&A.G.adj[W.beg[lo] + (g - W.excl[lo])]);
+        const uint32_t du = W.val[lo];
+        v = ent.x;
+        if ((int64_t)ent.y < R.ub_eff - (int64_t)du) {
+          C.trav += 1;
+          const uint32_t nd = du + ent.y;  // < min(ub, 2^32 - 1) by the window
+          if (nd < __ldcg(&A.dist[v])) {
+            const uint32_t old = atomicMin(&A.dist[v], nd);
+            ok = nd < old;
+            first = ok && old == EIC_INF;
+          }
+        }
+      }
+      C.improved += ok ? 1 : 0;
+      // into the local queue while it has room, else into the next round's queue (SAP)
+      const uint32_t m = __ballot_sync(EIC_FULL_MASK, ok);
+      const uint32_t cnt = __popc(m);
+      if (cnt && cnt <= kWarpStage - (lt - lh)) {
+        if (ok) lq[(lt + __popc(m & ((1u << lane) - 1u))) & (kWarpStage - 1)] = v;
+        lt += cnt;
+      } else if (cnt) {
+        bool sap = false;
+        if (ok) {
+          const uint32_t bit = 1u << (v & 31);
+          sap = !(atomicOr(&R.fbits[v >> 5], bit) & bit);
+        }
+        const uint32_t slot = warp_append(sap, R.qcnt_out);
+        if (sap) __stcg(&R.qout[slot], v);
+      }
+      warp_push(Fw, first, v);
+      __syncwarp();
+    }
+  }
+  warp_flush(Fw);
+  tl_block(A, 6, R.rid);
+}
+
 // Function 2 for the boundary <lb, ub> -> next pair <ub, ub + gap(ub)>, run by
 // one whole block. Candidates x_k = st0 + floor(k (st1 - st0) / ST_NUM) < ub;
 // D(x') = sumD(x') - sumD(ub), the degree sum of the settled vertices with
@@ -1250,7 +1362,7 @@ struct QueryShared {
 // The query loop of Algorithm 1 run by the A.nb blocks of one query: rounds
 // of a step (item phase, task phase), statistics pass, step boundary, until
 // termination. gen is the block's copy of the barrier generation.
-template <uint32_t kPullFast, uint32_t kRelaxIlp>
+template <uint32_t kPullFast, uint32_t kRelaxIlp, bool kFused = false>
 __device__ void run_query(const KArgs& A, QueryShared& Q, uint32_t& gen) {
   PhaseScr& P = Q.P;
   Stage& T = Q.T;
@@ -1322,7 +1434,10 @@ __device__ void run_query(const KArgs& A, QueryShared& Q, uint32_t& gen) {
       if (!L.pull_on) LL.pull_cnt = 0;
       const uint32_t nitems = round1 ? (LL.push_end - LL.push_beg) + LL.pull_cnt + LL.extra_s : L.cur_cnt;
       if (qb == 0 && threadIdx.x == 0) tl_mark(A, 8, nitems);  // diagnostic: the round's items
-      round_phase<kPullFast, kRelaxIlp>(A, R, LL, P.r, T, nitems, round1, qin, C);
+      if (kFused && !R.step1 && !round1 && nitems <= 32u * A.nb * (blockDim.x >> 5))
+        fused_round(A, R, P.r, T, nitems, qin, C);
+      else
+        round_phase<kPullFast, kRelaxIlp>(A, R, LL, P.r, T, nitems, round1, qin, C);
       if (!grid_barrier(&c->bar, &gen, A.nb, A.max_spin, &c->status)) {
         alive = false;
         break;
@@ -1522,6 +1637,15 @@ __global__ void __launch_bounds__(kMaxBlock, 2) k_eic(KArgs A) {
   __shared__ QueryShared Q;
   uint32_t gen = __ldcg(&A.ctl->bar.gen);
   run_query<kPullFastSingle, kRelaxIlpSingle>(A, Q, gen);
+}
+
+// The same query with fused rounds (bucket fusion), for graphs whose every
+// degree is at most heavy_min: road-like graphs, whose steps take many small
+// rounds.
+__global__ void __launch_bounds__(kMaxBlock, 2) k_eic_fused(KArgs A) {
+  __shared__ QueryShared Q;
+  uint32_t gen = __ldcg(&A.ctl->bar.gen);
+  run_query<kPullFastSingle, kRelaxIlpSingle, true>(A, Q, gen);
 }
 
 // Control block of a new query (one thread): the source's distance, the
@@ -2018,21 +2142,31 @@ struct DeviceGuard {
   ~DeviceGuard() { cudaSetDevice(prev); }
 };
 
-int launch_shape(Workspace* ws, int block) {
-  if (ws->grid && ws->block == block) return EIC_OK;
+// The cooperative grid of the query kernel (k_eic, or k_eic_fused), cached
+// per workspace for the block size last used.
+int launch_shape(Workspace* ws, int block, bool fused) {
+  int& grid = fused ? ws->grid_fused : ws->grid;
+  int& cached = fused ? ws->block_fused : ws->block;
+  if (grid && cached == block) return EIC_OK;
   int dev = 0, sms = 0, per_sm = 0, coop = 0;
   EIC_CUDA_TRY(cudaGetDevice(&dev));
   EIC_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   EIC_CUDA_TRY(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
   if (!coop) return EIC_ECUDA;
-  EIC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_eic, block, 0));
+  EIC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fused ? k_eic_fused : k_eic, block, 0));
   if (per_sm < 1) return EIC_ECUDA;
-  ws->grid = sms * per_sm;
-  ws->block = block;
+  grid = sms * per_sm;
+  cached = block;
   return EIC_OK;
 }
 
-KArgs make_args(eic_graph* g, uint32_t s, uint32_t* dist, const eic_params& p, int* status_out) {
+// Fused rounds (bucket fusion) apply to graphs whose every degree is at most
+// heavy_min, unless the caller turns them off.
+bool use_fused(const eic_graph* g, const eic_params& p) {
+  return g->dg.max_deg <= p.heavy_min && !(p.flags & EIC_FLAG_NO_FUSE);
+}
+
+KArgs make_args(eic_graph* g, uint32_t s, uint32_t* dist, const eic_params& p, int* status_out, int grid) {
   Workspace& w = g->ws;
   KArgs A;
   A.G = g->dg;
@@ -2072,7 +2206,7 @@ KArgs make_args(eic_graph* g, uint32_t s, uint32_t* dist, const eic_params& p, i
   A.trace_cap = kTraceCap;
   A.timeline = nullptr;
   A.timeline_cap = 0;
-  A.nb = (uint32_t)w.grid;
+  A.nb = (uint32_t)grid;
   return A;
 }
 
@@ -2081,12 +2215,14 @@ int enqueue_query(eic_graph* g, uint32_t s, uint32_t* dist, uint32_t* parent, co
                   cudaStream_t st, bool timeline = false, cudaEvent_t ev0 = nullptr, cudaEvent_t ev1 = nullptr) {
   Workspace& w = g->ws;
   const int block = p.block_threads ? (int)p.block_threads : kDefaultBlock;
-  int rc = launch_shape(&w, block);
+  const bool fused = use_fused(g, p);
+  int rc = launch_shape(&w, block, fused);
   if (rc) return rc;
+  const int grid = fused ? w.grid_fused : w.grid;
   EIC_CUDA_TRY(cudaMemsetAsync(w.idist, 0xFF, (uint64_t)g->dg.ni * 4, st));
   EIC_CUDA_TRY(cudaMemsetAsync(w.sbits, 0, ((uint64_t)g->dg.ni / 32 + 2) * 4, st));
   EIC_CUDA_TRY(cudaMemsetAsync(w.fbits, 0, 2 * ((uint64_t)g->dg.ni / 32 + 2) * 4, st));
-  KArgs A = make_args(g, s, dist, p, status_out);
+  KArgs A = make_args(g, s, dist, p, status_out, grid);
   if (timeline) {
     A.timeline = w.timeline;
     A.timeline_cap = kTimelineCap;
@@ -2095,9 +2231,10 @@ int enqueue_query(eic_graph* g, uint32_t s, uint32_t* dist, uint32_t* parent, co
   EIC_CUDA_TRY(cudaGetLastError());
   void* args[] = {&A};
   if (ev0) EIC_CUDA_TRY(cudaEventRecord(ev0, st));
-  EIC_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)k_eic, dim3(w.grid), dim3(block), args, 0, st));
+  EIC_CUDA_TRY(cudaLaunchCooperativeKernel(fused ? (const void*)k_eic_fused : (const void*)k_eic, dim3(grid),
+                                           dim3(block), args, 0, st));
   if (ev1) EIC_CUDA_TRY(cudaEventRecord(ev1, st));
-  k_output<<<4 * w.grid, 256, 0, st>>>(g->dg, w.idist, s, dist);
+  k_output<<<4 * grid, 256, 0, st>>>(g->dg, w.idist, s, dist);
   EIC_CUDA_TRY(cudaGetLastError());
   if (parent) {
     k_parent<<<1024, 256, 0, st>>>(g->dg, w.idist, s, parent);

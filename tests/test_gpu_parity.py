@@ -156,6 +156,48 @@ def test_parent_output():
         assert np.array_equal(eic.to_host_u32(par), og.parent(int(s), d))
 
 
+def test_fused_rounds_exact_with_fewer_rounds():
+    """Graphs whose degrees are all <= heavy_min run fused rounds (bucket
+    fusion): the distances and the step trace equal the oracle's, with or
+    without fusion, and fusion takes fewer grid-wide rounds."""
+    for wl in (G.road(96, seed=35, wmax=4095, nsources=2), G.road(128, seed=36, wmax=255, nsources=2)):
+        g, og = _pair(wl)
+        assert g.max_deg <= 32
+        for s in wl.sources:
+            s = int(s)
+            want, _ = og.dijkstra(s)
+            _, _, otrace, _ = og.eic(s)
+            keys = ("lb", "ub", "st", "gap_lb", "sumd_lb", "highd_lb", "settled")
+            rounds = []
+            for p in (None, eic.default_params(flags=eic.FLAG_NO_FUSE)):
+                d, rc, info = eic.sssp(g, s, params=p, stats=True, trace_cap=1 << 14)
+                assert rc == 0 and np.array_equal(eic.to_host_u32(d), want)
+                assert [{k: r[k] for k in keys} for r in info["trace"]] == [{k: r[k] for k in keys} for r in otrace]
+                rounds.append(info["rounds"])
+            assert rounds[0] < rounds[1], rounds
+
+
+def test_fused_rounds_local_queue_overflow():
+    """Degree-24 graphs (a union of random perfect matchings, unit and small
+    weights): a warp's wave improves more vertices than its local queue holds,
+    and the rest goes to the next round's queue; still exact."""
+    rng = np.random.default_rng(37)
+    n, k = 8192, 24
+    src, dst = [], []
+    for _ in range(k):
+        perm = rng.permutation(n).astype(np.uint32)
+        src.append(perm[0::2])
+        dst.append(perm[1::2])
+    src, dst = np.concatenate(src), np.concatenate(dst)
+    for w in (np.ones(src.size, np.uint32), rng.integers(1, 9, src.size).astype(np.uint32)):
+        g = eic.Graph(n, src, dst, w)
+        og = O.Graph(n, src, dst, w)
+        assert g.max_deg <= 32
+        for s in (0, 4097):
+            d, rc, _ = eic.sssp(g, s)
+            assert rc == 0 and np.array_equal(eic.to_host_u32(d), og.dijkstra(s)[0])
+
+
 def test_host_output_arrays():
     """dist and parent in page-locked host memory are written directly by the
     query; pageable host memory is rejected before any launch."""
