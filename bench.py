@@ -48,6 +48,9 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--scale", type=int, default=25, help="Kronecker scale of the workload")
+    ap.add_argument("--road", type=int, default=0, metavar="SIDE",
+                    help="time a SIDE^2 road-like grid (weights [1,4095]) instead of the Kronecker workload "
+                         "(for profiling the fused-round kernel)")
     ap.add_argument("--sources", type=int, default=64)
     ap.add_argument("--cpu-sample", type=int, default=1, help="oracle queries timed for cpu_baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -171,11 +174,16 @@ class ClockSampler:
         return out
 
 
-def make_workload(scale: int, nsources: int, rank: int = 0):
+def make_workload(scale: int, nsources: int, rank: int = 0, road: int = 0):
     """The resident graph (the same on every rank) and this rank's sources
     (replicas draw their own, so N ranks process N x nsources queries)."""
     from paper_2506_19349_gb300 import graphgen
 
+    if road:
+        wl = graphgen.road(road, seed=3, wmax=4095, nsources=nsources)
+        if rank:
+            wl.sources = graphgen.pick_sources(wl.n, wl.src, wl.dst, nsources, 3 + 1000 * rank, "largest")
+        return wl
     return graphgen.kron(scale, seed=2, nsources=nsources, source_seed=2 + 1000 * rank)
 
 
@@ -208,9 +216,12 @@ def whole_job_gteps(edges_all_ranks_per_step: float, steps: int, max_ms: float) 
     return edges_all_ranks_per_step * steps / (max_ms * 1e-3) / 1e9
 
 
-def workload_config(wl, scale, nsources):
-    return {"workload": f"kron{scale}: RMAT(0.57,0.19,0.19,0.05) scale {scale} edgefactor 16, ids permuted, "
-                        f"weights uniform [1,255], {nsources} sources uniform over non-isolated vertices",
+def workload_config(wl, scale, nsources, road=0):
+    desc = (f"road{road}: {road}^2 grid, 4-neighbour, 10% of edges deleted, 2% diagonal shortcuts, weights uniform "
+            f"[1,4095], {nsources} sources from the largest component" if road else
+            f"kron{scale}: RMAT(0.57,0.19,0.19,0.05) scale {scale} edgefactor 16, ids permuted, "
+            f"weights uniform [1,255], {nsources} sources uniform over non-isolated vertices")
+    return {"workload": desc,
             "n": int(wl.n), "tuples": int(wl.num_tuples), "queries_per_step": nsources,
             "l2": "inputs larger than L2 (CSR of the resident graph)", "path": "plain single-source, one "
                                                                           "persistent launch per query"}
@@ -241,7 +252,7 @@ def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return
-    wl = make_workload(args.scale, args.sources)
+    wl = make_workload(args.scale, args.sources, road=args.road)
     import oracle
 
     og = oracle.Graph(wl.n, wl.src, wl.dst, wl.w)
@@ -259,7 +270,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "GTEPS", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
-            "data": "synthetic", "config": workload_config(wl, args.scale, args.sources),
+            "data": "synthetic", "config": workload_config(wl, args.scale, args.sources, args.road),
             "cpu_baseline": {"value": value, "unit": "GTEPS", "cores": 1, "kind": "oracle",
                              "sample": f"one binary-heap Dijkstra query per step on kron{args.scale} (CPU "
                                        f"oracle), sources cycling through the workload's list"},
@@ -604,7 +615,7 @@ def main():
     import paper_2506_19349_gb300 as eic
 
     t0 = time.perf_counter()
-    wl = make_workload(args.scale, args.sources, rank)
+    wl = make_workload(args.scale, args.sources, rank, args.road)
     gen_s = time.perf_counter() - t0
     stream = torch.cuda.current_stream()
     torch.cuda.synchronize()
@@ -739,16 +750,17 @@ def main():
             "metric": METRIC, "value": value, "unit": "GTEPS", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-            "config": workload_config(wl, args.scale, q) | {"m": int(m_edges), "m_c_mean": statistics.mean(m_c),
+            "config": workload_config(wl, args.scale, q, args.road) | {"m": int(m_edges), "m_c_mean": statistics.mean(m_c),
                                                             "build_s": build_s, "generate_s": gen_s},
             "latency_ms": {"p50": q_sorted[len(q_sorted) // 2], "p99": q_sorted[min(len(q_sorted) - 1,
                                                                                       int(0.99 * len(q_sorted)))],
                            "mean": statistics.mean(q_ms)},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak,
-                         "traffic": MEASURED_TRAFFIC.get((args.scale, kernel_sources_sha256())),
+                         "traffic": None if args.road else MEASURED_TRAFFIC.get((args.scale, kernel_sources_sha256())),
                          "peak_kind": peak_kind,
-                         "kernel": "k_eic (one launch per query; CUDA events around its launch)",
+                         "kernel": ("k_eic_fused" if args.road else "k_eic") +
+                                   " (one launch per query; CUDA events around its launch)",
                          "kernel_ms_mean": statistics.mean(k_ms), "alg_bytes_mean": statistics.mean(b_alg)},
             "cpu_baseline": cpu, "clocks": clocks, "e2e": e2e, "gpu_launches": 3 * q * args.steps,
             "counters_mean": {k: statistics.mean(inf[k] for inf in all_infos)

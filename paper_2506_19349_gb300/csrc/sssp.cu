@@ -170,6 +170,7 @@ struct S2Scr {
   unsigned long long ring[kShRing];
 };
 
+constexpr uint32_t kGapPar = 256;   // distinct degrees up to which the boundary evaluates Eq. 1-3 for each
 constexpr uint32_t kStBins = 1920;  // Function 2 candidate bins held in shared memory (ST_NUM + 2 at most)
 
 struct S3Scr {
@@ -731,10 +732,20 @@ __device__ void task_phase(const KArgs& A, const RoundCtx& R, uint32_t ntasks, S
       uint2 ent[2];
       uint32_t dv[2], nd[2], old[2];
       bool act[2], ok[2];
+      if (!(tk.beg & 1u)) {  // the task starts on a 16-byte boundary: a lane loads its two entries as one pair
+        const uint32_t j = 2 * lane;
+        uint4 pr = make_uint4(0u, 0u, 0u, 0u);
+        if (j < tk.len) pr = ld_stream4(reinterpret_cast<const uint4*>(A.G.adj + tk.beg + j));  // (2 spare entries)
+        act[0] = j < tk.len;
+        act[1] = j + 1 < tk.len;
+        ent[0] = make_uint2(pr.x, pr.y);
+        ent[1] = act[1] ? make_uint2(pr.z, pr.w) : make_uint2(0u, 0u);
+      } else {
 #pragma unroll
-      for (uint32_t h = 0; h < 2; ++h) {
-        act[h] = lane + 32 * h < tk.len;
-        ent[h] = act[h] ? ld_stream(&A.G.adj[tk.beg + lane + 32 * h]) : make_uint2(0u, 0u);
+        for (uint32_t h = 0; h < 2; ++h) {
+          act[h] = lane + 32 * h < tk.len;
+          ent[h] = act[h] ? ld_stream(&A.G.adj[tk.beg + lane + 32 * h]) : make_uint2(0u, 0u);
+        }
       }
 #pragma unroll
       for (uint32_t h = 0; h < 2; ++h) dv[h] = act[h] ? __ldcg(&A.dist[ent[h].x]) : 0u;
@@ -1129,12 +1140,13 @@ __device__ int64_t block_compute_st(const KArgs& A, S3Scr& S, int64_t ub, uint64
 // statistics pass: sumD(ub), highD(ub), gap(ub) (Eq. 1-3), termination
 // (Algorithm 1), computeST (Function 2) and the push/pull sets of the next
 // step's Function 1. Publishes the new control values before the grid barrier.
-template <bool kExactInline>
+template <bool kExactInline, bool kParGap>
 __device__ void step_boundary(const KArgs& A, PhaseScr& P, BState& B, const Local& L, uint32_t rounds_in_step) {
   Ctl* c = A.ctl;
   __shared__ int64_t sh_i[8];
   __shared__ uint64_t sh_u[4];
   __shared__ uint32_t sh_flag[2];
+  __shared__ int64_t sh_gap[kGapPar];
   const DevGraph& G = A.G;
   const int64_t lb = L.lb, ub = L.ub;
   const uint32_t k = L.step;
@@ -1180,6 +1192,13 @@ __device__ void step_boundary(const KArgs& A, PhaseScr& P, BState& B, const Loca
   __syncthreads();
   const uint64_t sumd_ub = sh_u[0];
   uint32_t highd_ub;
+  // With few distinct degrees (road-like graphs: the fused kernel), Eq. 1-3 is
+  // evaluated for every value highD can take (each distinct degree) by the
+  // other warps while warp 0 finds highD: the double-precision chain of Eq. 2
+  // is long on this GPU, and it then runs beside highD instead of after it.
+  const bool gap_par = kParGap && G.D <= kGapPar && blockDim.x >= 32 + G.D;
+  if (gap_par && threadIdx.x >= 32 && threadIdx.x < 32 + G.D)
+    sh_gap[threadIdx.x - 32] = dev_gap(sumd_ub, G.dvals[threadIdx.x - 32], G.two_m, A.alpha, A.beta, G.rtow);
   if (G.D <= 32 * kWarpHighdPer) {  // one warp, no block barriers
     if (threadIdx.x < 32) {
       const uint32_t h = warp_highd(A.hist, G.dvals, G.D);
@@ -1199,7 +1218,9 @@ __device__ void step_boundary(const KArgs& A, PhaseScr& P, BState& B, const Loca
     return;
   }
   if (threadIdx.x == 0) {
-    const int64_t gap_raw = dev_gap(sumd_ub, highd_ub, G.two_m, A.alpha, A.beta, G.rtow);
+    // highD is a distinct degree (its rank from drank) or 0 (empty set: gap maxW(G, 1))
+    const int64_t gap_raw = gap_par && highd_ub > 0 ? sh_gap[__ldg(&G.drank[highd_ub])]
+                                                    : dev_gap(sumd_ub, highd_ub, G.two_m, A.alpha, A.beta, G.rtow);
     if (k == 1) B.st0 = ub;
     if (B.st1 < 0 && sumd_ub <= G.m) B.st1 = ub;
     sh_i[1] = gap_raw;
@@ -1609,7 +1630,7 @@ __device__ void run_query(const KArgs& A, QueryShared& Q, uint32_t& gen) {
           tl_mark(A, 4, L.rid);
         }
         __syncthreads();
-        if (sh_last) step_boundary<(kRelaxIlp >= 2)>(A, P, B, L, rin);  // (the single-query shape inlines)
+        if (sh_last) step_boundary<(kRelaxIlp >= 2), kFused>(A, P, B, L, rin);  // (the single-query shape inlines)
         if (threadIdx.x == 0) tl_mark(A, 5, L.rid);
       }
     }
