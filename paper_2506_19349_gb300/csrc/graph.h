@@ -60,7 +60,14 @@ struct BatchQuery {
   uint32_t s;
   uint32_t ring_mask, ring_shift, task_cap;
   uint32_t gap_shift, heavy_min;  // step-width scaling and window-class threshold for this query's graph
+  uint32_t fuse;                  // 1: fused rounds (every degree of the graph <= heavy_min)
 };
+
+// Fused rounds (bucket fusion) apply to a graph whose every degree is at most
+// heavy_min (no window becomes a grid task), unless the caller turns them off.
+inline bool fuse_ok(const DevGraph& G, uint32_t heavy_min, uint32_t flags) {
+  return G.max_deg <= heavy_min && !(flags & EIC_FLAG_NO_FUSE);
+}
 
 // Scratch of one block group, reused by every query the group runs.
 struct BatchSlot {

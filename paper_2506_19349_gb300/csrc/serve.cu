@@ -365,6 +365,7 @@ int eic_server_create(const eic_graph* const* graphs, uint32_t num_graphs, const
     q.task_cap = (uint32_t)(G.two_m / kHeavyMinFloor + 2);
     q.gap_shift = pr.gap_shift;
     q.heavy_min = pr.heavy_min;
+    q.fuse = fuse_ok(G, pr.heavy_min, pr.flags) ? 1u : 0u;
     hq.push_back(q);
     caps.ni = std::max<uint64_t>(caps.ni, G.ni);
     caps.two_m = std::max<uint64_t>(caps.two_m, G.two_m);

@@ -93,6 +93,7 @@ struct KArgs {
   unsigned long long* timeline;  // NULL unless the caller asked for it
   uint32_t timeline_cap;
   uint32_t nb;  // blocks working on this query: the grid, or one block group of a batch
+  uint32_t fuse;  // fused rounds for this query (kernels that decide per query)
 };
 
 // Index of the block within the blocks that work on its query.
@@ -1383,7 +1384,8 @@ struct QueryShared {
 // The query loop of Algorithm 1 run by the A.nb blocks of one query: rounds
 // of a step (item phase, task phase), statistics pass, step boundary, until
 // termination. gen is the block's copy of the barrier generation.
-template <uint32_t kPullFast, uint32_t kRelaxIlp, bool kFused = false>
+// kFuse: 0 no fused rounds, 1 fused rounds, 2 as A.fuse says (per query).
+template <uint32_t kPullFast, uint32_t kRelaxIlp, uint32_t kFuse = 0>
 __device__ void run_query(const KArgs& A, QueryShared& Q, uint32_t& gen) {
   PhaseScr& P = Q.P;
   Stage& T = Q.T;
@@ -1455,7 +1457,8 @@ __device__ void run_query(const KArgs& A, QueryShared& Q, uint32_t& gen) {
       if (!L.pull_on) LL.pull_cnt = 0;
       const uint32_t nitems = round1 ? (LL.push_end - LL.push_beg) + LL.pull_cnt + LL.extra_s : L.cur_cnt;
       if (qb == 0 && threadIdx.x == 0) tl_mark(A, 8, nitems);  // diagnostic: the round's items
-      if (kFused && !R.step1 && !round1 && nitems <= 32u * A.nb * (blockDim.x >> 5))
+      if ((kFuse == 1 || (kFuse == 2 && A.fuse)) && !R.step1 && !round1 &&
+          nitems <= 32u * A.nb * (blockDim.x >> 5))
         fused_round(A, R, P.r, T, nitems, qin, C);
       else
         round_phase<kPullFast, kRelaxIlp>(A, R, LL, P.r, T, nitems, round1, qin, C);
@@ -1630,7 +1633,7 @@ __device__ void run_query(const KArgs& A, QueryShared& Q, uint32_t& gen) {
           tl_mark(A, 4, L.rid);
         }
         __syncthreads();
-        if (sh_last) step_boundary<(kRelaxIlp >= 2), kFused>(A, P, B, L, rin);  // (the single-query shape inlines)
+        if (sh_last) step_boundary<(kRelaxIlp >= 2), kFuse == 1>(A, P, B, L, rin);  // (the single-query shape inlines)
         if (threadIdx.x == 0) tl_mark(A, 5, L.rid);
       }
     }
@@ -1666,7 +1669,7 @@ __global__ void __launch_bounds__(kMaxBlock, 2) k_eic(KArgs A) {
 __global__ void __launch_bounds__(kMaxBlock, 2) k_eic_fused(KArgs A) {
   __shared__ QueryShared Q;
   uint32_t gen = __ldcg(&A.ctl->bar.gen);
-  run_query<kPullFastSingle, kRelaxIlpSingle, true>(A, Q, gen);
+  run_query<kPullFastSingle, kRelaxIlpSingle, 1>(A, Q, gen);
 }
 
 // Control block of a new query (one thread): the source's distance, the
@@ -1877,10 +1880,11 @@ __global__ void __launch_bounds__(kMaxBlock, 2) k_eic_batch(BatchArgs P) {
       sA.timeline = nullptr;
       sA.timeline_cap = 0;
       sA.nb = P.nb;
+      sA.fuse = bq.fuse;
     }
     __syncthreads();
     if (!query_setup(sA, gen)) break;
-    run_query<kPullFastGroup, kRelaxIlpGroup>(sA, Q, gen);
+    run_query<kPullFastGroup, kRelaxIlpGroup, 2>(sA, Q, gen);
     __syncthreads();
     if (ld_volatile_int(&c->status) != 0) break;
     query_output(sA);
@@ -2062,10 +2066,11 @@ __global__ void __launch_bounds__(kMaxBlock, 2) k_eic_serve(ServeArgs P) {
       sA.timeline = nullptr;
       sA.timeline_cap = 0;
       sA.nb = P.nb;
+      sA.fuse = bq.fuse;
     }
     __syncthreads();
     if (!query_setup(sA, gen)) break;
-    run_query<kPullFastGroup, kRelaxIlpGroup>(sA, Q, gen);
+    run_query<kPullFastGroup, kRelaxIlpGroup, 2>(sA, Q, gen);
     __syncthreads();
     if (ld_volatile_int(&c->status) != 0) break;
     query_output(sA);
@@ -2183,9 +2188,7 @@ int launch_shape(Workspace* ws, int block, bool fused) {
 
 // Fused rounds (bucket fusion) apply to graphs whose every degree is at most
 // heavy_min, unless the caller turns them off.
-bool use_fused(const eic_graph* g, const eic_params& p) {
-  return g->dg.max_deg <= p.heavy_min && !(p.flags & EIC_FLAG_NO_FUSE);
-}
+bool use_fused(const eic_graph* g, const eic_params& p) { return fuse_ok(g->dg, p.heavy_min, p.flags); }
 
 KArgs make_args(eic_graph* g, uint32_t s, uint32_t* dist, const eic_params& p, int* status_out, int grid) {
   Workspace& w = g->ws;
@@ -2228,6 +2231,7 @@ KArgs make_args(eic_graph* g, uint32_t s, uint32_t* dist, const eic_params& p, i
   A.timeline = nullptr;
   A.timeline_cap = 0;
   A.nb = (uint32_t)grid;
+  A.fuse = 0;  // (the single-query kernels fix it: k_eic_fused or k_eic)
   return A;
 }
 
@@ -2652,6 +2656,7 @@ int batch_create(const eic_graph* const* graphs, const uint32_t* sources, uint32
     q.task_cap = (uint32_t)(G.two_m / kHeavyMinFloor + 2);
     q.gap_shift = p.gap_shift;
     q.heavy_min = p.heavy_min;
+    q.fuse = fuse_ok(G, p.heavy_min, p.flags) ? 1u : 0u;
     b->hq.push_back(q);
     b->order.push_back(i);
     b->qgraph.push_back(graphs[i]);
@@ -2818,7 +2823,10 @@ int eic_batch_tune(eic_batch* b, void* stream, eic_batch_config* best) {
     // one configuration: a warm-up run, then a timed one when the warm-up was
     // within 2x of the best so far
     auto trial = [&](uint32_t g, uint32_t block, uint32_t hm, double* ms_out) -> int {
-      for (auto& q : b->hq) q.heavy_min = hm;
+      for (auto& q : b->hq) {
+        q.heavy_min = hm;
+        q.fuse = fuse_ok(q.G, hm, b->p.flags) ? 1u : 0u;
+      }
       b->p.heavy_min = hm;
       int r = batch_upload(b);
       if (r) return r;
@@ -2910,7 +2918,10 @@ int eic_batch_tune(eic_batch* b, void* stream, eic_batch_config* best) {
     if ((rc = trial(best_g, 256, best_hm, nullptr))) return rc;
     (void)hm0;
     // keep the winner; the scratch shrinks to its group count
-    for (auto& q : b->hq) q.heavy_min = best_hm;
+    for (auto& q : b->hq) {
+      q.heavy_min = best_hm;
+      q.fuse = fuse_ok(q.G, best_hm, b->p.flags) ? 1u : 0u;
+    }
     b->p.heavy_min = best_hm;
     if ((rc = batch_upload(b))) return rc;
     if (b->pool == &b->own && b->own.count > best_g) b->own.release();
@@ -3087,6 +3098,7 @@ extern "C" int eic_sssp_noalloc(const eic_graph* gc, uint32_t source, uint32_t* 
   A.timeline = nullptr;
   A.timeline_cap = 0;
   A.nb = (uint32_t)nd.grid;
+  A.fuse = 0;
   // Once anything is enqueued, every return waits for the stream first: the
   // next call may reuse the scratch only when this call's work has finished.
   auto enqueue = [&]() -> int {
