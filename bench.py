@@ -76,7 +76,7 @@ def dist_env():
 KERNEL_SOURCES = ("paper_2506_19349_gb300/csrc/sssp.cu", "paper_2506_19349_gb300/csrc/common.cuh",
                   "paper_2506_19349_gb300/csrc/graph.h", "paper_2506_19349_gb300/csrc/stats.cuh", "include/eic.h")
 MEASURED_TRAFFIC = {  # {(scale, kernel code sha256): bytes per launch}
-    (25, "fb2bd6ec0da9963fe6bc2ac839c953b05330327c0e7edeb20ccc491043ed9ea4"): 6445003648,
+    (25, "0554e1b1cce68c861c4acb6c46b0432dd69662332c604de63f4d705945855160"): 6624003840,
 }
 
 
