@@ -454,7 +454,6 @@ __device__ void round_phase(const KArgs& A, const RoundCtx& R, const Local& L, R
     uint32_t u = 0, val = EIC_INF, b = 0, len = 0, mode = kModePush;
     uint32_t pfast = EIC_INF;       // best pull candidate of the lane's vertex
     bool plong = false;             // its prefix is longer than kPullFast entries
-    uint32_t pbeg = 0, pend = 0;    // the rest of its row, scanned by the warp
     if (kind != kKindNone) {
       if (kind == kKindVertex) {  // frontier vertex (or the source, once)
         u = rec.x;
@@ -517,38 +516,14 @@ __device__ void round_phase(const KArgs& A, const RoundCtx& R, const Local& L, R
                 pfast = min(pfast, (uint32_t)(dvv + ent[k].y));
             }
           }
-          if (plong) {
-            pbeg = z.z + kPullFast;
-            pend = z.w;
+          if (plong) {  // the prefix goes on past the lane's entries: find its end, then the rest
+                        // is a window like a push window (the warp's concatenation, or grid tasks)
+            b = z.z + kPullFast;
+            const uint32_t e = pull_bound > (int64_t)A.G.maxw ? z.w : gallop_w(A.G.adj, b, z.w, pull_bound);
+            len = e - b;
           }
         }
       }
-    }
-    // long pull prefixes, one lane's row at a time: coalesced 32-entry chunks
-    // while the whole chunk is below the bound (no search for the prefix end)
-    for (uint32_t lm = __ballot_sync(EIC_FULL_MASK, plong); lm; lm &= lm - 1) {
-      const uint32_t sl = __ffs(lm) - 1;
-      const uint32_t cb = __shfl_sync(EIC_FULL_MASK, pbeg, sl), ce = __shfl_sync(EIC_FULL_MASK, pend, sl);
-      uint32_t best = EIC_INF;
-      for (uint32_t base = cb; base < ce; base += 32) {
-        const uint32_t j = base + lane;
-        bool in = false;
-        if (j < ce) {
-          const uint2 e2 = ld_stream(&A.G.adj[j]);
-          in = (int64_t)e2.y < pull_bound;
-          if (in) {
-            C.trav += 1;
-            C.pulls += 1;
-            const uint32_t dv = __ldcg(&A.dist[e2.x]);
-            const int64_t dvv = dv;
-            if (dv != EIC_INF && dvv >= R.st && dvv < R.lb && dvv + e2.y < R.ub)
-              best = min(best, (uint32_t)(dvv + e2.y));
-          }
-        }
-        if (!__all_sync(EIC_FULL_MASK, in || j >= ce)) break;  // the prefix ended in this chunk
-      }
-      for (int o = 16; o > 0; o >>= 1) best = min(best, __shfl_xor_sync(EIC_FULL_MASK, best, o));
-      if (lane == sl) pfast = min(pfast, best);
     }
     if (len > A.heavy_min) {
       emit_tasks(A, R, T, b, len, u, mode == kModePull ? kNone : val);
