@@ -198,6 +198,28 @@ def test_fused_rounds_local_queue_overflow():
             assert rc == 0 and np.array_equal(eic.to_host_u32(d), og.dijkstra(s)[0])
 
 
+def test_output_alignment_and_ragged_tail():
+    """The output kernel writes 16-byte groups when dist is 16-byte aligned and
+    one value at a time otherwise; n = 4k + 3 leaves a ragged tail."""
+    n = 4 * 257 + 3
+    src = np.arange(n - 1, dtype=np.uint32)
+    w = (src % 5 + 1).astype(np.uint32)
+    extra_s = np.array([0, 10, 500], np.uint32)
+    extra_d = np.array([n - 1, n - 2, n - 5], np.uint32)
+    s_all, d_all = np.concatenate([src, extra_s]), np.concatenate([src + 1, extra_d])
+    w_all = np.concatenate([w, np.array([7, 3, 11], np.uint32)])
+    g = eic.Graph(n, s_all, d_all, w_all)
+    og = O.Graph(n, s_all, d_all, w_all)
+    for s in (0, n - 1, n - 3):
+        want, _ = og.dijkstra(s)
+        for off in (0, 1, 3):
+            buf = torch.full((n + 4,), 7, dtype=torch.int32, device="cuda")
+            d = buf[off:off + n]
+            _, rc, _ = eic.sssp(g, s, dist=d)
+            assert rc == 0 and np.array_equal(eic.to_host_u32(d), want), (s, off)
+            assert (buf[:off] == 7).all() and (buf[off + n:] == 7).all()
+
+
 def test_host_output_arrays():
     """dist and parent in page-locked host memory are written directly by the
     query; pageable host memory is rejected before any launch."""
