@@ -921,9 +921,11 @@ __device__ __noinline__ int64_t block_st_exact_call(const KArgs& A, S3Scr& S, in
 
 // A fused round: the FUSED local iterations of Section 4.1 (bucket fusion),
 // for graphs in which no window is longer than heavy_min (every degree <=
-// heavy_min, so there are no grid tasks), in the rounds after a step's first.
-// Each warp takes up to 32 of the round's frontier vertices and relaxes their
-// windows; every vertex it improves goes into the warp's local queue (shared
+// heavy_min, so there are no grid tasks), in every round of a step after the
+// first (and its first round too when the step has no pull). Each warp takes
+// up to 32 of the round's frontier vertices (or of the push set, whose windows
+// start at their cursors) and relaxes their windows; every vertex it improves
+// goes into the warp's local queue (shared
 // memory, kWarpStage entries) and is relaxed by the same warp in its next
 // wave, with the distance it has then, until the local queue is empty. The
 // warps advance independently, with no grid barrier between waves: the round
@@ -934,8 +936,8 @@ __device__ __noinline__ int64_t block_st_exact_call(const KArgs& A, S3Scr& S, in
 // A wave is one chain of dependent loads (the vertex record, its row, the
 // neighbours' distances, the atomicMin) where a plain round adds a grid
 // barrier and the next round's item fetch.
-__device__ void fused_round(const KArgs& A, const RoundCtx& R, RoundScr& S, Stage& T, uint32_t nitems,
-                            const uint32_t* qin, Counters& C) {
+__device__ void fused_round(const KArgs& A, const RoundCtx& R, const Local& L, RoundScr& S, Stage& T,
+                            uint32_t nitems, bool round1, const uint32_t* qin, Counters& C) {
   const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
   const uint32_t gwarp = qblock(A) * (blockDim.x >> 5) + warp;
   WarpScr& W = S.w[warp];
@@ -943,41 +945,71 @@ __device__ void fused_round(const KArgs& A, const RoundCtx& R, RoundScr& S, Stag
   uint32_t lh = 0, lt = 0;    // its head and tail (warp-uniform)
   WarpList Fw = {T.wf[warp], 0u, R.first_cnt, R.first_list};
   const uint32_t i0 = gwarp * 32;
-  if (i0 < nitems) {
+  // a step's first round (no pull): the warp's first wave is its share of the
+  // push set (and the source, once); later rounds: of the round's queue
+  const uint32_t np = round1 ? L.push_end - L.push_beg : 0;
+  uint32_t nseed = round1 && i0 < nitems ? min(32u, nitems - i0) : 0u;
+  if (!round1 && i0 < nitems) {
     if (i0 + lane < nitems) lq[lane] = ld_list(&qin[i0 + lane]);
     lt = min(32u, nitems - i0);
   }
   __syncwarp();
-  while (lh != lt) {
-    const uint32_t k = min(32u, lt - lh);
-    const bool has = lane < k;
-    const uint32_t u = has ? lq[(lh + lane) & (kWarpStage - 1)] : 0u;
-    __syncwarp();
-    lh += k;
-    uint32_t d = EIC_INF, rb = 0, re = 0, len = 0;
-    if (has) {
-      d = __ldcg(&A.dist[u]);
-      rb = __ldg(&A.G.row[u]);
-      re = __ldg(&A.G.row[u + 1]);
+  while (nseed || lh != lt) {
+    uint32_t d = EIC_INF, b = 0, len = 0;
+    bool vertex = false;  // a frontier vertex (or the source): its window starts at its row
+    uint32_t u = 0;
+    if (nseed) {
+      const uint32_t i = i0 + lane;
+      if (lane < nseed && i < np) {  // push set entry: settled, lb0 <= dist <= st (Function 1)
+        const uint32_t idx = L.push_beg + i;
+        d = ld_list(&A.sd[idx]);
+        const uint2 rr = ld_list2(&A.srow[idx]);
+        if ((int64_t)d >= R.lb0 && (int64_t)d <= R.st && !(d > 0 && rr.y - rr.x == 1)) {
+          C.frontier += 1;
+          const uint32_t cur = ld_list(&A.scur[idx]);
+          b = cur == kNone ? lower_bound_w(A.G.adj, rr.x, rr.y, R.lb - (int64_t)d)
+                           : gallop_w(A.G.adj, rr.x + cur, rr.y, R.lb - (int64_t)d);
+          const uint32_t e = gallop_w(A.G.adj, b, rr.y, R.ub_eff - (int64_t)d);
+          __stcg(&A.scur[idx], e - rr.x);
+          len = e - b;
+        }
+      } else if (lane < nseed) {  // the source, once
+        u = L.s_int;
+        vertex = true;
+      }
+      nseed = 0;
+    } else {
+      const uint32_t k = min(32u, lt - lh);
+      if (lane < k) {
+        u = lq[(lh + lane) & (kWarpStage - 1)];
+        vertex = true;
+      }
+      __syncwarp();
+      lh += k;
     }
-    // d >= lb: the window is the row's prefix with weight < ub - d; rows are
-    // short, so the whole row is read and filtered (a search only for rows
-    // that keep a cursor)
-    if (has && d != EIC_INF && !(d > 0 && re - rb == 1)) {  // Paths excludes leaves (Algorithm 1)
-      C.frontier += 1;
-      const int64_t hi = R.ub_eff - (int64_t)d;
-      if (hi > 0) {
-        len = re - rb;
-        if (re - rb > kCursorMin) {
-          const uint32_t e = gallop_w(A.G.adj, rb, re, hi);
-          __stcg(&A.cursor[u], e - rb);
-          len = e - rb;
+    if (vertex) {
+      d = __ldcg(&A.dist[u]);
+      const uint32_t rb = __ldg(&A.G.row[u]), re = __ldg(&A.G.row[u + 1]);
+      // d >= lb: the window is the row's prefix with weight < ub - d; rows are
+      // short, so the whole row is read and filtered (a search only for rows
+      // that keep a cursor)
+      if (d != EIC_INF && !(d > 0 && re - rb == 1)) {  // Paths excludes leaves (Algorithm 1)
+        C.frontier += 1;
+        const int64_t hi = R.ub_eff - (int64_t)d;
+        if (hi > 0) {
+          b = rb;
+          len = re - rb;
+          if (re - rb > kCursorMin) {
+            const uint32_t e = gallop_w(A.G.adj, rb, re, hi);
+            __stcg(&A.cursor[u], e - rb);
+            len = e - rb;
+          }
         }
       }
     }
     const uint32_t incl = warp_incl_scan(len);
     const uint32_t total = __shfl_sync(EIC_FULL_MASK, incl, 31);
-    W.beg[lane] = rb;
+    W.beg[lane] = b;
     W.excl[lane] = incl - len;
     W.val[lane] = d;
     __syncwarp();
@@ -1432,9 +1464,9 @@ __device__ void run_query(const KArgs& A, QueryShared& Q, uint32_t& gen) {
       if (!L.pull_on) LL.pull_cnt = 0;
       const uint32_t nitems = round1 ? (LL.push_end - LL.push_beg) + LL.pull_cnt + LL.extra_s : L.cur_cnt;
       if (qb == 0 && threadIdx.x == 0) tl_mark(A, 8, nitems);  // diagnostic: the round's items
-      if ((kFuse == 1 || (kFuse == 2 && A.fuse)) && !R.step1 && !round1 &&
+      if ((kFuse == 1 || (kFuse == 2 && A.fuse)) && !R.step1 && (!round1 || !LL.pull_on) &&
           nitems <= 32u * A.nb * (blockDim.x >> 5))
-        fused_round(A, R, P.r, T, nitems, qin, C);
+        fused_round(A, R, LL, P.r, T, nitems, round1, qin, C);
       else
         round_phase<kPullFast, kRelaxIlp>(A, R, LL, P.r, T, nitems, round1, qin, C);
       if (!grid_barrier(&c->bar, &gen, A.nb, A.max_spin, &c->status)) {
