@@ -176,7 +176,7 @@ constexpr uint32_t kStBins = 1920;  // Function 2 candidate bins held in shared 
 
 struct S3Scr {
   unsigned long long part[kMaxBlock];
-  double bp[32];
+  unsigned long long bp[32];  // per warp: the best profit's key (see block_argmax)
   uint32_t bk[32];
   unsigned long long bins[kStBins];
 };
@@ -793,41 +793,54 @@ __device__ void task_phase(const KArgs& A, const RoundCtx& R, uint32_t ntasks, S
 }
 
 // The first candidate index with the largest positive profit over the block
-// (ties: the smaller index), or 0xFFFFFFFF when no profit is positive.
+// (ties: the smaller index), or 0xFFFFFFFF when no profit is positive. The
+// reduction compares integer keys: a positive double's bit pattern orders as
+// the double does, and a profit <= 0 gets key 0 (this GPU's double-precision
+// units are few, and a block of double compares queues on them).
 __device__ __forceinline__ uint32_t block_argmax(S3Scr& S, double best, uint32_t bk) {
   const uint32_t t = threadIdx.x, nt = blockDim.x;
+  unsigned long long key = best > 0.0 ? (unsigned long long)__double_as_longlong(best) : 0ull;
+  if (!key) bk = 0xFFFFFFFFu;
   for (int o = 16; o > 0; o >>= 1) {
-    double ob = __shfl_down_sync(EIC_FULL_MASK, best, o);
-    uint32_t ok = __shfl_down_sync(EIC_FULL_MASK, bk, o);
-    if (ob > best || (ob == best && ok < bk)) {
-      best = ob;
-      bk = ok;
+    const unsigned long long ok = __shfl_down_sync(EIC_FULL_MASK, key, o);
+    const uint32_t okk = __shfl_down_sync(EIC_FULL_MASK, bk, o);
+    if (ok > key || (ok == key && okk < bk)) {
+      key = ok;
+      bk = okk;
     }
   }
   __syncthreads();
   if ((t & 31) == 0) {
-    S.bp[t >> 5] = best;
+    S.bp[t >> 5] = key;
     S.bk[t >> 5] = bk;
   }
   __syncthreads();
   if (t < 32) {
-    best = t < (nt >> 5) ? S.bp[t] : 0.0;
+    key = t < (nt >> 5) ? S.bp[t] : 0ull;
     bk = t < (nt >> 5) ? S.bk[t] : 0xFFFFFFFFu;
     for (int o = 16; o > 0; o >>= 1) {
-      double ob = __shfl_down_sync(EIC_FULL_MASK, best, o);
-      uint32_t ok = __shfl_down_sync(EIC_FULL_MASK, bk, o);
-      if (ob > best || (ob == best && ok < bk)) {
-        best = ob;
-        bk = ok;
+      const unsigned long long ok = __shfl_down_sync(EIC_FULL_MASK, key, o);
+      const uint32_t okk = __shfl_down_sync(EIC_FULL_MASK, bk, o);
+      if (ok > key || (ok == key && okk < bk)) {
+        key = ok;
+        bk = okk;
       }
     }
-    if (t == 0) S.bk[0] = bk;
+    if (t == 0) S.bk[0] = key ? bk : 0xFFFFFFFFu;
   }
   __syncthreads();
   const uint32_t k = S.bk[0];
   __syncthreads();
   return k;
 }
+
+// The candidate grid x_k = st0 + floor(k span / ST_NUM) (Section 4.1): a
+// shift when ST_NUM is a power of two (the paper's 1024), else a division.
+__device__ __forceinline__ int64_t st_candidate(uint32_t k, uint64_t span, uint32_t st_num, uint32_t sh, int64_t st0) {
+  const uint64_t q = (uint64_t)k * span;
+  return st0 + (int64_t)(sh < 32 ? q >> sh : q / st_num);
+}
+
 
 // Function 2 for weights of 2^20 and above (one block), with D(x') summed
 // exactly from the settled list: over the entries of the steps
@@ -894,8 +907,9 @@ __device__ __forceinline__ int64_t block_st_exact(const KArgs& A, S3Scr& S, int6
   __syncthreads();
   double best = 0.0;
   uint32_t bk = 0xFFFFFFFFu;
+  const uint32_t gsh = (A.st_num & (A.st_num - 1)) == 0 ? __ffs(A.st_num) - 1 : 32u;
   for (uint32_t k = t; k <= A.st_num; k += nt) {
-    const int64_t x = st0 + (int64_t)(((uint64_t)k * span) / A.st_num);
+    const int64_t x = st_candidate(k, span, A.st_num, gsh, st0);
     if (x >= ub) continue;
     const uint64_t q = x >= wl ? (uint64_t)k + 1 : 0;
     const unsigned long long dsum = sh ? bins[q] : __ldcg(&bins[q]);
@@ -907,7 +921,7 @@ __device__ __forceinline__ int64_t block_st_exact(const KArgs& A, S3Scr& S, int6
   }
   const uint32_t k = block_argmax(S, best, bk);
   if (k == 0xFFFFFFFFu) return ub;
-  return st0 + (int64_t)(((uint64_t)k * span) / A.st_num);
+  return st_candidate(k, span, A.st_num, gsh, st0);
 }
 
 // The same out of line, for the batch and serving kernels: inlined there it
@@ -1092,12 +1106,14 @@ __device__ int64_t block_compute_st(const KArgs& A, S3Scr& S, int64_t ub, uint64
   }
   double best = 0.0;
   uint32_t bk = 0xFFFFFFFFu;
+  const uint64_t span = (uint64_t)(st1 - st0);
+  const uint32_t gsh = (A.st_num & (A.st_num - 1)) == 0 ? __ffs(A.st_num) - 1 : 32u;
   for (uint32_t k = t; k <= A.st_num; k += nt) {
-    const int64_t x = st0 + (int64_t)(((uint64_t)k * (uint64_t)(st1 - st0)) / A.st_num);
+    const int64_t x = st_candidate(k, span, A.st_num, gsh, st0);
     if (x >= ub) continue;
     const int64_t xc = x > ub - maxw ? x : ub - maxw;
     if (k > 0) {  // the profit depends on x' only: the first candidate of each x' decides the argmax
-      const int64_t xp = st0 + (int64_t)(((uint64_t)(k - 1) * (uint64_t)(st1 - st0)) / A.st_num);
+      const int64_t xp = st_candidate(k - 1, span, A.st_num, gsh, st0);
       if ((xp > ub - maxw ? xp : ub - maxw) == xc) continue;
     }
     const uint64_t q0 = (uint64_t)xc >> sh;
@@ -1110,38 +1126,9 @@ __device__ int64_t block_compute_st(const KArgs& A, S3Scr& S, int64_t ub, uint64
       bk = k;
     }
   }
-  for (int o = 16; o > 0; o >>= 1) {
-    double ob = __shfl_down_sync(EIC_FULL_MASK, best, o);
-    uint32_t ok = __shfl_down_sync(EIC_FULL_MASK, bk, o);
-    if (ob > best || (ob == best && ok < bk)) {
-      best = ob;
-      bk = ok;
-    }
-  }
-  __syncthreads();
-  if ((t & 31) == 0) {
-    S.bp[t >> 5] = best;
-    S.bk[t >> 5] = bk;
-  }
-  __syncthreads();
-  if (t < 32) {
-    best = t < (nt >> 5) ? S.bp[t] : 0.0;
-    bk = t < (nt >> 5) ? S.bk[t] : 0xFFFFFFFFu;
-    for (int o = 16; o > 0; o >>= 1) {
-      double ob = __shfl_down_sync(EIC_FULL_MASK, best, o);
-      uint32_t ok = __shfl_down_sync(EIC_FULL_MASK, bk, o);
-      if (ob > best || (ob == best && ok < bk)) {
-        best = ob;
-        bk = ok;
-      }
-    }
-    if (t == 0) S.bk[0] = bk;
-  }
-  __syncthreads();
-  const uint32_t k = S.bk[0];
-  __syncthreads();
+  const uint32_t k = block_argmax(S, best, bk);
   if (k == 0xFFFFFFFFu) return ub;
-  return st0 + (int64_t)(((uint64_t)k * (uint64_t)(st1 - st0)) / A.st_num);
+  return st_candidate(k, span, A.st_num, gsh, st0);
 }
 
 // Step boundary, executed by block 0 once every block finished the
