@@ -397,7 +397,7 @@ int eic_server_destroy(eic_server* s);
  * Same result as eic_sssp (exact distances, paper's default parameters), but
  * the query's scratch (frontier queues, settled list, statistics, tasks,
  * control block) lives in one fixed-size device array inside libeic instead of
- * the graph's workspace. That array (about 15.5 MB) is held on every GPU where
+ * the graph's workspace. That array (about 13.4 MB) is held on every GPU where
  * the library is loaded, until the process exits. The call allocates nothing:
  * no cudaMalloc, cudaFree or allocating library routine; the caller supplies
  * the graph (created beforehand with eic_graph_create) and the output buffer.

@@ -35,6 +35,7 @@ struct DevGraph {
   const uint32_t* drank;  // [max_deg + 1] degree -> rank among distinct degrees (present ones)
   const uint32_t* dvals;  // [D] distinct degrees >= 1, ascending
   const uint32_t* dcnt0;  // [D] number of vertices with degree dvals[r]
+  const uint32_t* dfirst;  // [D] first internal id of degree dvals[r] (decreasing in r: ids run by degree descending)
   uint32_t D;
   const uint32_t* rtow;   // [EIC_RATIO_NUM] maxW(G, i / (RATIO_NUM - 1))
   const uint4* nz;        // [nz_count = ni] {internal id, smallest row weight, row begin, row end}, by (weight, id)
@@ -43,6 +44,21 @@ struct DevGraph {
   uint32_t nz_lt_len;
   uint32_t maxw, minw, max_deg, highd0;
 };
+
+// Rank (index into dvals) of internal vertex x's degree: internal ids run by
+// degree descending, so it is the smallest r with dfirst[r] <= x. A search in
+// a small table that stays in L1, in place of a random row[x], row[x + 1].
+__device__ __forceinline__ uint32_t degree_rank(const DevGraph& G, uint32_t x) {
+  uint32_t lo = 0, hi = G.D - 1;
+  while (lo < hi) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if (__ldg(&G.dfirst[mid]) <= x)
+      hi = mid;
+    else
+      lo = mid + 1;
+  }
+  return lo;
+}
 
 // ------------------------------------------------------------ warp helpers
 

@@ -306,6 +306,7 @@ void graph_free_arrays(eic_graph* g) {
   cudaFree(g->drank);
   cudaFree(g->dvals);
   cudaFree(g->dcnt0);
+  cudaFree(g->dfirst);
   cudaFree(g->rtow);
   cudaFree(g->nz);
   cudaFree(g->nz_lt);
@@ -522,6 +523,20 @@ int build(eic_graph* g, const uint32_t* src, const uint32_t* dst, const uint32_t
     k_degree_tables<<<grid_for(hlen), kThreads, 0, st>>>(dh, flags, pos, hlen, g->dvals, g->dcnt0, g->drank);
     k_highd0<<<1, 1024, 0, st>>>(g->dcnt0, g->dvals, D, small + 4);
     EIC_CUDA_TRY(cudaGetLastError());
+    // dfirst[r]: the first internal id of degree dvals[r] (ids by degree descending)
+    TRY(galloc(g, &g->dfirst, D));
+    if (D) {
+      std::vector<uint32_t> cnt(D), first(D);
+      EIC_CUDA_TRY(cudaMemcpyAsync(cnt.data(), g->dcnt0, (uint64_t)D * 4, cudaMemcpyDeviceToHost, st));
+      EIC_CUDA_TRY(cudaStreamSynchronize(st));
+      uint64_t acc = 0;
+      for (uint32_t r = D; r-- > 0;) {
+        first[r] = (uint32_t)acc;
+        acc += cnt[r];
+      }
+      EIC_CUDA_TRY(cudaMemcpyAsync(g->dfirst, first.data(), (uint64_t)D * 4, cudaMemcpyHostToDevice, st));
+      EIC_CUDA_TRY(cudaStreamSynchronize(st));
+    }
   }
 
   // 5c. every internal vertex with its smallest weight, ordered by (smallest
@@ -565,6 +580,7 @@ int build(eic_graph* g, const uint32_t* src, const uint32_t* dst, const uint32_t
   dg.drank = g->drank;
   dg.dvals = g->dvals;
   dg.dcnt0 = g->dcnt0;
+  dg.dfirst = g->dfirst;
   dg.D = D;
   dg.rtow = g->rtow;
   dg.nz = g->nz;

@@ -79,7 +79,6 @@ struct BatchSlot {
   uint32_t* sid;
   uint32_t* sd;
   uint32_t* scur;
-  uint2* srow;
   uint32_t* touched;
   uint32_t* sbits;
   uint32_t* hist;
@@ -98,7 +97,6 @@ struct Workspace {
   uint32_t* sid = nullptr;   // settled list: vertex
   uint32_t* sd = nullptr;    // settled list: final distance
   uint32_t* scur = nullptr;  // settled list: window cursor (offset in the row)
-  uint2* srow = nullptr;     // settled list: row begin, row end
   uint32_t* cursor = nullptr;
   uint32_t* touched = nullptr;
   uint32_t* sbits = nullptr;  // settled bitmap
@@ -127,6 +125,7 @@ struct eic_graph {
   uint32_t* drank = nullptr;
   uint32_t* dvals = nullptr;
   uint32_t* dcnt0 = nullptr;
+  uint32_t* dfirst = nullptr;
   uint32_t* rtow = nullptr;
   uint4* nz = nullptr;
   uint32_t* nz_lt = nullptr;

@@ -20,7 +20,7 @@ struct SlotCaps {
 
 // Byte offsets of one group's arrays inside its slot (256-byte aligned).
 struct SlotLayout {
-  uint64_t idist, fbits, cursor, q0, q1, sid, sd, scur, srow, touched, sbits, hist, ring, tasks, step_ub, step_off,
+  uint64_t idist, fbits, cursor, q0, q1, sid, sd, scur, touched, sbits, hist, ring, tasks, step_ub, step_off,
       ctl, bytes;
 };
 
@@ -41,7 +41,6 @@ inline SlotLayout slot_layout(const SlotCaps& c) {
   L.sid = take((n + 2) * 4);
   L.sd = take((n + 2) * 4);
   L.scur = take((n + 2) * 4);
-  L.srow = take((n + 2) * 8);
   L.touched = take((n + 1) * 4);
   L.sbits = take(words * 4);
   L.hist = take(((uint64_t)c.D + 1) * 4);
@@ -94,7 +93,6 @@ struct SlotPool {
       s.sid = (uint32_t*)(b + L.sid);
       s.sd = (uint32_t*)(b + L.sd);
       s.scur = (uint32_t*)(b + L.scur);
-      s.srow = (uint2*)(b + L.srow);
       s.touched = (uint32_t*)(b + L.touched);
       s.sbits = (uint32_t*)(b + L.sbits);
       s.hist = (uint32_t*)(b + L.hist);

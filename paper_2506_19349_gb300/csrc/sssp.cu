@@ -12,8 +12,8 @@
 //                a vertex into the next frontier only if its bit was clear
 //   cursor[n]    where the last window relaxed from a vertex ended (offset in its row)
 //   q[2][n]      frontier queues, one per round parity
-//   sid/sd/scur/srow  settled list in settling order (vertex, final distance,
-//                window cursor, row bounds); step k owns [step_off[k], step_off[k+1])
+//   sid/sd/scur  settled list in settling order (vertex, final distance, window
+//                cursor); step k owns [step_off[k], step_off[k+1])
 //   touched[n]   first-step insertions (the first step's ub shrinks, so its
 //                tentative distances >= the final ub are reset to +inf)
 //   sbits[n/32]  settled bitmap: the pull set of Function 1 is the unsettled part of
@@ -69,7 +69,6 @@ struct KArgs {
   uint32_t* sid;
   uint32_t* sd;
   uint32_t* scur;
-  uint2* srow;
   uint32_t* touched;
   uint32_t* sbits;  // settled bitmap
   uint32_t* hist;
@@ -435,18 +434,19 @@ __device__ void round_phase(const KArgs& A, const RoundCtx& R, const Local& L, R
   // vertex or the source, {dist, row begin, row end} for the push set (from
   // the settled list), the nz entry for a listed pull. Records are loaded one
   // warp iteration ahead, a frontier vertex's queue entry two ahead.
-  auto fetch_id = [&](uint32_t ii) -> uint32_t { return !round1 && ii < nlisted ? ld_list(&qin[ii]) : 0u; };
+  // (the push set's settled-list vertices come in the same way, two ahead)
+  auto fetch_id = [&](uint32_t ii) -> uint32_t {
+    if (ii >= nlisted) return 0u;
+    if (!round1) return ld_list(&qin[ii]);
+    return ii < np ? ld_list(&A.sid[L.push_beg + ii]) : 0u;
+  };
   auto fetch = [&](uint32_t ii, uint32_t id) -> uint4 {
     if (ii >= nlisted) return make_uint4(0u, 0u, 0u, 0u);
     if (!round1 || ii >= npp) {  // frontier vertex (or the source, once)
       const uint32_t u = round1 ? L.s_int : id;
       return make_uint4(u, __ldcg(&A.dist[u]), __ldg(&A.G.row[u]), __ldg(&A.G.row[u + 1]));
     }
-    if (ii < np) {
-      const uint32_t idx = L.push_beg + ii;
-      const uint2 rr = ld_list2(&A.srow[idx]);
-      return make_uint4(ld_list(&A.sd[idx]), rr.x, rr.y, 0u);
-    }
+    if (ii < np) return make_uint4(ld_list(&A.sd[L.push_beg + ii]), __ldg(&A.G.row[id]), __ldg(&A.G.row[id + 1]), 0u);
     return ld_stream4(&A.G.nz[ii - np]);
   };
   // one warp iteration: each lane's item (kind kKindNone: no item)
@@ -872,7 +872,7 @@ __device__ __forceinline__ int64_t block_st_exact(const KArgs& A, S3Scr& S, int6
   for (uint32_t i = s_beg + t; i < send; i += nt) {
     const int64_t d = ld_list(&A.sd[i]);
     if (d < wl) continue;
-    const uint2 rr = ld_list2(&A.srow[i]);
+    const uint32_t dg = __ldg(&A.G.dvals[degree_rank(A.G, ld_list(&A.sid[i]))]);
     uint64_t cnt;  // how many x_k are <= d: the k with k (st1 - st0) < (d - st0 + 1) ST_NUM
     if (d < st0)
       cnt = 0;
@@ -880,7 +880,7 @@ __device__ __forceinline__ int64_t block_st_exact(const KArgs& A, S3Scr& S, int6
       cnt = nbins - 1;
     else
       cnt = min(((uint64_t)(d - st0 + 1) * A.st_num + span - 1) / span, nbins - 1);
-    atomicAdd(&bins[cnt], (unsigned long long)(rr.y - rr.x));
+    atomicAdd(&bins[cnt], (unsigned long long)dg);
   }
   __syncthreads();
   // suffix sums: chunk totals, a scan over the chunks, then within the chunks
@@ -977,7 +977,8 @@ __device__ void fused_round(const KArgs& A, const RoundCtx& R, const Local& L, R
       if (lane < nseed && i < np) {  // push set entry: settled, lb0 <= dist <= st (Function 1)
         const uint32_t idx = L.push_beg + i;
         d = ld_list(&A.sd[idx]);
-        const uint2 rr = ld_list2(&A.srow[idx]);
+        const uint32_t x = ld_list(&A.sid[idx]);
+        const uint2 rr = make_uint2(__ldg(&A.G.row[x]), __ldg(&A.G.row[x + 1]));
         if ((int64_t)d >= R.lb0 && (int64_t)d <= R.st && !(d > 0 && rr.y - rr.x == 1)) {
           C.frontier += 1;
           const uint32_t cur = ld_list(&A.scur[idx]);
@@ -1245,7 +1246,6 @@ __device__ void step_boundary(const KArgs& A, PhaseScr& P, BState& B, const Loca
       A.sid[scnt] = L.s_int;
       A.sd[scnt] = 0;
       A.scur[scnt] = kNone;
-      A.srow[scnt] = make_uint2(G.row[L.s_int], G.row[L.s_int + 1]);
       ++scnt;
       extra = 1;
     }
@@ -1523,7 +1523,7 @@ __device__ void run_query(const KArgs& A, QueryShared& Q, uint32_t& gen) {
       for (uint32_t base = lbeg + qb * blockDim.x; base < lend; base += nthreads) {
         const uint32_t idx = base + threadIdx.x;
         bool take = false;
-        uint32_t x = 0, d = 0, xrb = 0, xre = 0;
+        uint32_t x = 0, d = 0, r = EIC_INF, dg = 0;
         uint32_t xcur = 0;
         if constexpr (kRelaxIlp >= 2) {
           xcur = xnext;
@@ -1535,8 +1535,8 @@ __device__ void run_query(const KArgs& A, QueryShared& Q, uint32_t& gen) {
           else
             x = ld_list(&list[idx]);
           d = __ldcg(&A.dist[x]);
-          xrb = __ldg(&A.G.row[x]);
-          xre = __ldg(&A.G.row[x + 1]);
+          r = degree_rank(A.G, x);  // (the degree from the id: no random row read)
+          dg = __ldg(&A.G.dvals[r]);
           take = true;
           if (step1 && d64(d) >= L.ub) {  // first step: keep only what is final
             if (x != L.s_int) __stcg(&A.dist[x], EIC_INF);
@@ -1549,23 +1549,20 @@ __device__ void run_query(const KArgs& A, QueryShared& Q, uint32_t& gen) {
             __stcg(&A.sid[slot], x);
             __stcg(&A.sd[slot], d);
             __stcg(&A.scur[slot], kNone);  // the first step's windows used a larger ub
-            __stcg(&A.srow[slot], make_uint2(xrb, xre));
           }
         }
         if (take) {
           atomicOr(&A.sbits[x >> 5], 1u << (x & 31));
-          const uint32_t dg = xre - xrb;
           if (!step1) {
             __stcg(&A.sd[idx], d);
             __stcg(&A.scur[idx], dg > kCursorMin ? __ldcg(&A.cursor[x]) : kNone);
-            __stcg(&A.srow[idx], make_uint2(xrb, xre));
           }
           bdeg += dg;
           bmax = d > bmax ? d : bmax;
           bany = 1;
         }
-        // degree histogram (degree-0 vertices, an isolated source, carry no rank)
-        const uint32_t r = take && xre > xrb ? __ldg(&A.G.drank[xre - xrb]) : EIC_INF;
+        // degree histogram (internal vertices all have degree >= 1)
+        if (!take) r = EIC_INF;
         if (r < (uint32_t)kShRanks)
           atomicAdd(&S.hist[r], 1u);
         else if (r != EIC_INF)
@@ -1578,13 +1575,13 @@ __device__ void run_query(const KArgs& A, QueryShared& Q, uint32_t& gen) {
                                  : EIC_INF;
         if (ring_narrow) {
           const uint32_t rg = __match_any_sync(EIC_FULL_MASK, slot);
-          const uint32_t sum = __reduce_add_sync(rg, rk ? xre - xrb : 0u);
+          const uint32_t sum = __reduce_add_sync(rg, rk ? dg : 0u);
           if (rk && lane_id() == (uint32_t)__ffs(rg) - 1) atomicAdd(&S.ring[slot], (unsigned long long)sum);
         } else if (rk) {
           if (ring_sh)
-            atomicAdd(&S.ring[slot], (unsigned long long)(xre - xrb));
+            atomicAdd(&S.ring[slot], (unsigned long long)dg);
           else
-            atomicAdd(&A.ring[slot], (unsigned long long)(xre - xrb));
+            atomicAdd(&A.ring[slot], (unsigned long long)dg);
         }
       }
       __syncthreads();
@@ -1847,7 +1844,6 @@ __global__ void __launch_bounds__(kMaxBlock, 2) k_eic_batch(BatchArgs P) {
       sA.sid = W.sid;
       sA.sd = W.sd;
       sA.scur = W.scur;
-      sA.srow = W.srow;
       sA.touched = W.touched;
       sA.sbits = W.sbits;
       sA.hist = W.hist;
@@ -2033,7 +2029,6 @@ __global__ void __launch_bounds__(kMaxBlock, 2) k_eic_serve(ServeArgs P) {
       sA.sid = W.sid;
       sA.sd = W.sd;
       sA.scur = W.scur;
-      sA.srow = W.srow;
       sA.touched = W.touched;
       sA.sbits = W.sbits;
       sA.hist = W.hist;
@@ -2198,7 +2193,6 @@ KArgs make_args(eic_graph* g, uint32_t s, uint32_t* dist, const eic_params& p, i
   A.sid = w.sid;
   A.sd = w.sd;
   A.scur = w.scur;
-  A.srow = w.srow;
   A.touched = w.touched;
   A.sbits = w.sbits;
   A.hist = w.hist;
@@ -2313,7 +2307,6 @@ void eic_ws_free(Workspace* w) {
   cudaFree(w->sid);
   cudaFree(w->sd);
   cudaFree(w->scur);
-  cudaFree(w->srow);
   cudaFree(w->cursor);
   cudaFree(w->touched);
   cudaFree(w->sbits);
@@ -2349,7 +2342,7 @@ int eic_ws_ensure(eic_graph* g, int) {
   w->n = G.ni;
   if ((rc = walloc(w, &w->idist, n)) || (rc = walloc(w, &w->fbits, 2 * (n / 32 + 2))) || (rc = walloc(w, &w->q[0], n)) || (rc = walloc(w, &w->q[1], n)) ||
       (rc = walloc(w, &w->sid, n + 2)) || (rc = walloc(w, &w->sd, n + 2)) ||
-      (rc = walloc(w, &w->scur, n + 2)) || (rc = walloc(w, &w->srow, n + 2)) || (rc = walloc(w, &w->cursor, n)) || (rc = walloc(w, &w->touched, n + 1)) || (rc = walloc(w, &w->sbits, n / 32 + 2)) ||
+      (rc = walloc(w, &w->scur, n + 2)) || (rc = walloc(w, &w->cursor, n)) || (rc = walloc(w, &w->touched, n + 1)) || (rc = walloc(w, &w->sbits, n / 32 + 2)) ||
       (rc = walloc(w, &w->hist, (uint64_t)G.D + 1)) || (rc = walloc(w, &w->ring, 1ull << w->ring_bits)) ||
       (rc = walloc(w, &w->tasks, w->task_cap)) || (rc = walloc(w, &w->step_ub, (uint64_t)kStepCap + 2)) ||
       (rc = walloc(w, &w->step_off, (uint64_t)kStepCap + 2)) || (rc = walloc(w, &w->trace, kTraceCap)) || (rc = walloc(w, &w->timeline, 2ull * kTimelineCap)) ||
@@ -2986,8 +2979,7 @@ constexpr uint64_t kNaQ1 = kNaQ0 + na_align(kNaN * 4);
 constexpr uint64_t kNaSid = kNaQ1 + na_align(kNaN * 4);
 constexpr uint64_t kNaSd = kNaSid + na_align((kNaN + 2) * 4);
 constexpr uint64_t kNaScur = kNaSd + na_align((kNaN + 2) * 4);
-constexpr uint64_t kNaSrow = kNaScur + na_align((kNaN + 2) * 4);
-constexpr uint64_t kNaTouched = kNaSrow + na_align((kNaN + 2) * 8);
+constexpr uint64_t kNaTouched = kNaScur + na_align((kNaN + 2) * 4);
 constexpr uint64_t kNaSbits = kNaTouched + na_align((kNaN + 1) * 4);
 constexpr uint64_t kNaHist = kNaSbits + na_align((kNaN / 32 + 2) * 4);
 constexpr uint64_t kNaRing = kNaHist + na_align(kNaD * 4);
@@ -2996,7 +2988,7 @@ constexpr uint64_t kNaStepUb = kNaTaskOff + na_align(kNaTasks * sizeof(Task));
 constexpr uint64_t kNaStepOff = kNaStepUb + na_align((kNaS + 2) * 8);
 constexpr uint64_t kNaCtl = kNaStepOff + na_align((kNaS + 2) * 4);
 constexpr uint64_t kNaBytes = kNaCtl + na_align(sizeof(Ctl));
-static_assert(kNaBytes > 15000000 && kNaBytes < 16000000, "the header states the scratch size as about 15.5 MB");
+static_assert(kNaBytes > 13000000 && kNaBytes < 14000000, "the header states the scratch size as about 13.4 MB");
 
 static __device__ __align__(256) unsigned char g_na_scratch[kNaBytes];
 
@@ -3065,7 +3057,6 @@ extern "C" int eic_sssp_noalloc(const eic_graph* gc, uint32_t source, uint32_t* 
   A.sid = (uint32_t*)(b + kNaSid);
   A.sd = (uint32_t*)(b + kNaSd);
   A.scur = (uint32_t*)(b + kNaScur);
-  A.srow = (uint2*)(b + kNaSrow);
   A.touched = (uint32_t*)(b + kNaTouched);
   A.sbits = (uint32_t*)(b + kNaSbits);
   A.hist = (uint32_t*)(b + kNaHist);
