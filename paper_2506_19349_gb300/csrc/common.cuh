@@ -36,6 +36,7 @@ struct DevGraph {
   const uint32_t* dvals;  // [D] distinct degrees >= 1, ascending
   const uint32_t* dcnt0;  // [D] number of vertices with degree dvals[r]
   const uint32_t* dfirst;  // [D] first internal id of degree dvals[r] (decreasing in r: ids run by degree descending)
+  const uint2* dhint;      // [ni / 4096 + 1] {rank of the block's last id, rank of its first id} per 4096 ids
   uint32_t D;
   const uint32_t* rtow;   // [EIC_RATIO_NUM] maxW(G, i / (RATIO_NUM - 1))
   const uint4* nz;        // [nz_count = ni] {internal id, smallest row weight, row begin, row end}, by (weight, id)
@@ -47,9 +48,11 @@ struct DevGraph {
 
 // Rank (index into dvals) of internal vertex x's degree: internal ids run by
 // degree descending, so it is the smallest r with dfirst[r] <= x. A search in
-// a small table that stays in L1, in place of a random row[x], row[x + 1].
+// a small table that stays in L1, narrowed to the ranks of x's block of 4096
+// ids, in place of a random row[x], row[x + 1].
 __device__ __forceinline__ uint32_t degree_rank(const DevGraph& G, uint32_t x) {
-  uint32_t lo = 0, hi = G.D - 1;
+  const uint2 h = __ldg(&G.dhint[x >> 12]);  // the ranks in x's block of 4096 ids: one rank in most blocks
+  uint32_t lo = h.x, hi = h.y;
   while (lo < hi) {
     const uint32_t mid = (lo + hi) >> 1;
     if (__ldg(&G.dfirst[mid]) <= x)

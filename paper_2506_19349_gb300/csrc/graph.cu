@@ -307,6 +307,7 @@ void graph_free_arrays(eic_graph* g) {
   cudaFree(g->dvals);
   cudaFree(g->dcnt0);
   cudaFree(g->dfirst);
+  cudaFree(g->dhint);
   cudaFree(g->rtow);
   cudaFree(g->nz);
   cudaFree(g->nz_lt);
@@ -537,6 +538,32 @@ int build(eic_graph* g, const uint32_t* src, const uint32_t* dst, const uint32_t
       EIC_CUDA_TRY(cudaMemcpyAsync(g->dfirst, first.data(), (uint64_t)D * 4, cudaMemcpyHostToDevice, st));
       EIC_CUDA_TRY(cudaStreamSynchronize(st));
     }
+    // dhint[b]: the ranks of ids 4096 b + 4095 and 4096 b (the range a rank search in block b needs)
+    const uint64_t nblk = (uint64_t)ni / 4096 + 1;
+    TRY(galloc(g, &g->dhint, nblk));
+    if (D) {
+      std::vector<uint32_t> first(D);
+      EIC_CUDA_TRY(cudaMemcpyAsync(first.data(), g->dfirst, (uint64_t)D * 4, cudaMemcpyDeviceToHost, st));
+      EIC_CUDA_TRY(cudaStreamSynchronize(st));
+      auto rank_of = [&](uint64_t x) -> uint32_t {  // the smallest r with first[r] <= x
+        uint32_t lo = 0, hi = D - 1;
+        while (lo < hi) {
+          const uint32_t mid = (lo + hi) / 2;
+          if (first[mid] <= x)
+            hi = mid;
+          else
+            lo = mid + 1;
+        }
+        return lo;
+      };
+      std::vector<uint2> hint(nblk);
+      for (uint64_t b = 0; b < nblk; ++b) {
+        const uint64_t x0 = b * 4096, x1 = std::min<uint64_t>(x0 + 4095, ni ? ni - 1 : 0);
+        hint[b] = make_uint2(rank_of(x1), rank_of(std::min<uint64_t>(x0, x1)));
+      }
+      EIC_CUDA_TRY(cudaMemcpyAsync(g->dhint, hint.data(), nblk * sizeof(uint2), cudaMemcpyHostToDevice, st));
+      EIC_CUDA_TRY(cudaStreamSynchronize(st));
+    }
   }
 
   // 5c. every internal vertex with its smallest weight, ordered by (smallest
@@ -581,6 +608,7 @@ int build(eic_graph* g, const uint32_t* src, const uint32_t* dst, const uint32_t
   dg.dvals = g->dvals;
   dg.dcnt0 = g->dcnt0;
   dg.dfirst = g->dfirst;
+  dg.dhint = g->dhint;
   dg.D = D;
   dg.rtow = g->rtow;
   dg.nz = g->nz;

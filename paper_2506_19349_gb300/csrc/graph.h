@@ -126,6 +126,7 @@ struct eic_graph {
   uint32_t* dvals = nullptr;
   uint32_t* dcnt0 = nullptr;
   uint32_t* dfirst = nullptr;
+  uint2* dhint = nullptr;
   uint32_t* rtow = nullptr;
   uint4* nz = nullptr;
   uint32_t* nz_lt = nullptr;
