@@ -76,7 +76,7 @@ def dist_env():
 KERNEL_SOURCES = ("paper_2506_19349_gb300/csrc/sssp.cu", "paper_2506_19349_gb300/csrc/common.cuh",
                   "paper_2506_19349_gb300/csrc/graph.h", "paper_2506_19349_gb300/csrc/stats.cuh", "include/eic.h")
 MEASURED_TRAFFIC = {  # {(scale, kernel code sha256): bytes per launch}
-    (25, "0554e1b1cce68c861c4acb6c46b0432dd69662332c604de63f4d705945855160"): 6624003840,
+    (25, "1078127eac2b377d4f1f974a8121df4850d843f371bf184d62c8713303211ee2"): 6085168832,
 }
 
 
