@@ -388,6 +388,27 @@ __device__ __forceinline__ void emit_tasks(const KArgs& A, const RoundCtx& R, St
 // in the first step the running min over high-degree vertices that becomes
 // ub (Algorithm 1). Warp-collective: every lane calls it; the appends go
 // through the warp's stages.
+// Sets v's bit in the round's insertion bitmap; true when this call set it.
+__device__ __forceinline__ bool claim_bit(const RoundCtx& R, uint32_t v) {
+  const uint32_t bit = 1u << (v & 31);
+  return !(atomicOr(&R.fbits[v >> 5], bit) & bit);
+}
+
+// After a relaxation: v into the next frontier when sap (its insertion bit was
+// set by this lane), into the first-reached list when it had no distance, and
+// the first step's ub candidate when v's degree is at least highD(0).
+__device__ __forceinline__ void on_claimed(const KArgs& A, const RoundCtx& R, bool ok, bool sap, uint32_t v,
+                                           uint32_t nd, uint32_t old, Counters& C, WarpList& Q, WarpList& F) {
+  const bool first = ok && old == EIC_INF;
+  warp_push(Q, sap, v);
+  warp_push(F, first, v);
+  if (R.step1 && ok) {
+    const uint32_t dg = __ldg(&A.G.row[v + 1]) - __ldg(&A.G.row[v]);
+    if (dg >= A.G.highd0) atomicMin(&A.ctl->ub_cand, nd);
+  }
+  C.improved += ok ? 1 : 0;
+}
+
 __device__ __forceinline__ void on_success(const KArgs& A, const RoundCtx& R, bool ok, uint32_t v, uint32_t nd,
                                            uint32_t old, Counters& C, WarpList& Q, WarpList& F) {
   bool sap = false;
@@ -543,7 +564,7 @@ __device__ void round_phase(const KArgs& A, const RoundCtx& R, const Local& L, R
     for (uint32_t g0 = 0; g0 < total; g0 += 32 * kRelaxIlp) {
       uint32_t own[kRelaxIlp], dv[kRelaxIlp], nd[kRelaxIlp], old[kRelaxIlp];
       uint2 ent[kRelaxIlp];
-      bool act[kRelaxIlp], push[kRelaxIlp], ok[kRelaxIlp];
+      bool act[kRelaxIlp], push[kRelaxIlp], ok[kRelaxIlp], sap[kRelaxIlp];
 #pragma unroll
       for (uint32_t h = 0; h < kRelaxIlp; ++h) {
         const uint32_t g = g0 + h * 32 + lane;
@@ -573,13 +594,21 @@ __device__ void round_phase(const KArgs& A, const RoundCtx& R, const Local& L, R
 #pragma unroll
       for (uint32_t h = 0; h < kRelaxIlp; ++h) {
         ok[h] = false;
+        sap[h] = false;
         nd[h] = 0;
         old[h] = 0;
         if (push[h]) {
           C.trav += 1;
           nd[h] = W.val[own[h]] + ent[h].y;  // inside [lb, min(ub, 2^32-1)) by the window bounds
           if (nd[h] < dv[h]) {
+            // The insertion bit is claimed together with the atomicMin, not
+            // after it. Should the atomicMin find a value <= nd, another
+            // relaxation lowered dist[v] in this round after the read above
+            // (distances only fall, and the round sees every earlier round's
+            // writes), so v is in the next frontier either way and whichever
+            // lane set the bit queues it.
             old[h] = atomicMin(&A.dist[ent[h].x], nd[h]);
+            sap[h] = claim_bit(R, ent[h].x);
             ok[h] = nd[h] < old[h];
           }
         } else if (act[h]) {
@@ -591,7 +620,7 @@ __device__ void round_phase(const KArgs& A, const RoundCtx& R, const Local& L, R
         }
       }
 #pragma unroll
-      for (uint32_t h = 0; h < kRelaxIlp; ++h) on_success(A, R, ok[h], ent[h].x, nd[h], old[h], C, Qw, Fw);
+      for (uint32_t h = 0; h < kRelaxIlp; ++h) on_claimed(A, R, ok[h], sap[h], ent[h].x, nd[h], old[h], C, Qw, Fw);
     }
     __syncwarp();
     bool pok = false;
@@ -707,7 +736,7 @@ __device__ void task_phase(const KArgs& A, const RoundCtx& R, uint32_t ntasks, S
     if (kAhead && tk.d != kNone) {  // push, both entries' loads in flight together
       uint2 ent[2];
       uint32_t dv[2], nd[2], old[2];
-      bool act[2], ok[2];
+      bool act[2], ok[2], sap[2];
       if (!(tk.beg & 1u)) {  // the task starts on a 16-byte boundary: a lane loads its two entries as one pair
         const uint32_t j = 2 * lane;
         uint4 pr = make_uint4(0u, 0u, 0u, 0u);
@@ -728,18 +757,20 @@ __device__ void task_phase(const KArgs& A, const RoundCtx& R, uint32_t ntasks, S
 #pragma unroll
       for (uint32_t h = 0; h < 2; ++h) {
         ok[h] = false;
+        sap[h] = false;
         old[h] = 0;
         nd[h] = tk.d + ent[h].y;
         if (act[h]) {
           C.trav += 1;
-          if (nd[h] < dv[h]) {
+          if (nd[h] < dv[h]) {  // the insertion bit claimed together with the atomicMin, as in the rounds
             old[h] = atomicMin(&A.dist[ent[h].x], nd[h]);
+            sap[h] = claim_bit(R, ent[h].x);
             ok[h] = nd[h] < old[h];
           }
         }
       }
 #pragma unroll
-      for (uint32_t h = 0; h < 2; ++h) on_success(A, R, ok[h], ent[h].x, nd[h], old[h], C, Qw, Fw);
+      for (uint32_t h = 0; h < 2; ++h) on_claimed(A, R, ok[h], sap[h], ent[h].x, nd[h], old[h], C, Qw, Fw);
     } else if (tk.d != kNone) {  // push
 #pragma unroll
       for (uint32_t h = 0; h < 2; ++h) {
