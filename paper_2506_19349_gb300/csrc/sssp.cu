@@ -474,6 +474,7 @@ __device__ void round_phase(const KArgs& A, const RoundCtx& R, const Local& L, R
   auto step_items = [&](const uint4 rec, const uint32_t i, const uint32_t kind) {
     uint32_t u = 0, val = EIC_INF, b = 0, len = 0, mode = kModePush;
     uint32_t pfast = EIC_INF;       // best pull candidate of the lane's vertex
+    uint32_t du = EIC_INF;          // the pulled vertex's distance when its pull started
     bool plong = false;             // its prefix is longer than kPullFast entries
     if (kind != kKindNone) {
       if (kind == kKindVertex) {  // frontier vertex (or the source, once)
@@ -514,6 +515,7 @@ __device__ void round_phase(const KArgs& A, const RoundCtx& R, const Local& L, R
         const uint32_t bits = L.pull_sweep ? z.y : __ldcg(&A.sbits[u >> 5]);
         if (!((bits >> (u & 31)) & 1u)) {  // unsettled: its row's first kPullFast entries, together
           const uint32_t rl = z.w - z.z;
+          du = __ldcg(&A.dist[u]);
           uint2 ent[kPullFast];
   #pragma unroll
           for (uint32_t k = 0; k < kPullFast; ++k)
@@ -623,14 +625,15 @@ __device__ void round_phase(const KArgs& A, const RoundCtx& R, const Local& L, R
       for (uint32_t h = 0; h < kRelaxIlp; ++h) on_claimed(A, R, ok[h], sap[h], ent[h].x, nd[h], old[h], C, Qw, Fw);
     }
     __syncwarp();
-    bool pok = false;
+    bool pok = false, psap = false;
     uint32_t pold = 0;
     const uint32_t pbest = W.val[lane];
-    if (mode == kModePull && pbest != EIC_INF) {
+    if (mode == kModePull && pbest < du) {
       pold = atomicMin(&A.dist[u], pbest);
+      psap = claim_bit(R, u);
       pok = pbest < pold;
     }
-    on_success(A, R, pok, u, pbest, pold, C, Qw, Fw);
+    on_claimed(A, R, pok, psap, u, pbest, pold, C, Qw, Fw);
     __syncwarp();
   };
   const uint32_t stride = nwarps * 32;
