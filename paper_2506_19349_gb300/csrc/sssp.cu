@@ -628,7 +628,8 @@ __device__ void round_phase(const KArgs& A, const RoundCtx& R, const Local& L, R
     bool pok = false, psap = false;
     uint32_t pold = 0;
     const uint32_t pbest = W.val[lane];
-    if (mode == kModePull && pbest < du) {
+    if (mode == kModePull && pbest < du) {  // du was read in this round: the insertion bit is
+                                            // claimed with the atomicMin, as for pushes
       pold = atomicMin(&A.dist[u], pbest);
       psap = claim_bit(R, u);
       pok = pbest < pold;
