@@ -23,6 +23,8 @@
 // Read-only view of a device-resident graph (preprocessing of Section 4.1).
 // Vertices have internal ids 0..ni-1: the non-isolated vertices ordered by
 // (degree descending, original id); orig2int/int2orig translate.
+constexpr uint32_t kCursorMin = 16;  // rows longer than this keep a window cursor
+
 struct DevGraph {
   uint32_t n;             // vertices in the caller's numbering
   uint32_t ni;            // internal vertices (degree >= 1)
@@ -44,6 +46,7 @@ struct DevGraph {
   const uint32_t* nz_lt;  // [nz_lt_len] nz_lt[t] = number of nz entries with smallest weight < t
   uint32_t nz_lt_len;
   uint32_t maxw, minw, max_deg, highd0;
+  uint32_t nlong;         // internal vertices of degree > kCursorMin: ids [0, nlong), the rows with a window cursor
 };
 
 // Rank (index into dvals) of internal vertex x's degree: internal ids run by

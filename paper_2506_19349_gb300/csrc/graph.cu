@@ -503,7 +503,7 @@ int build(eic_graph* g, const uint32_t* src, const uint32_t* dst, const uint32_t
 
   // 5b. distinct-degree tables and highD(0)
   const uint32_t hlen = maxdeg + 1;
-  uint32_t D = 0;
+  uint32_t D = 0, nlong = 0;
   {
     uint32_t *dh, *flags;
     uint64_t* pos;
@@ -527,13 +527,15 @@ int build(eic_graph* g, const uint32_t* src, const uint32_t* dst, const uint32_t
     // dfirst[r]: the first internal id of degree dvals[r] (ids by degree descending)
     TRY(galloc(g, &g->dfirst, D));
     if (D) {
-      std::vector<uint32_t> cnt(D), first(D);
+      std::vector<uint32_t> cnt(D), first(D), vals(D);
       EIC_CUDA_TRY(cudaMemcpyAsync(cnt.data(), g->dcnt0, (uint64_t)D * 4, cudaMemcpyDeviceToHost, st));
+      EIC_CUDA_TRY(cudaMemcpyAsync(vals.data(), g->dvals, (uint64_t)D * 4, cudaMemcpyDeviceToHost, st));
       EIC_CUDA_TRY(cudaStreamSynchronize(st));
       uint64_t acc = 0;
       for (uint32_t r = D; r-- > 0;) {
         first[r] = (uint32_t)acc;
         acc += cnt[r];
+        if (vals[r] > kCursorMin) nlong = (uint32_t)acc;  // ids [0, acc) have degree >= vals[r]
       }
       EIC_CUDA_TRY(cudaMemcpyAsync(g->dfirst, first.data(), (uint64_t)D * 4, cudaMemcpyHostToDevice, st));
       EIC_CUDA_TRY(cudaStreamSynchronize(st));
@@ -609,6 +611,7 @@ int build(eic_graph* g, const uint32_t* src, const uint32_t* dst, const uint32_t
   dg.dcnt0 = g->dcnt0;
   dg.dfirst = g->dfirst;
   dg.dhint = g->dhint;
+  dg.nlong = nlong;
   dg.D = D;
   dg.rtow = g->rtow;
   dg.nz = g->nz;

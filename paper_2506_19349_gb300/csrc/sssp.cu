@@ -101,7 +101,6 @@ __device__ __forceinline__ uint32_t qblock(const KArgs& A) { return blockIdx.x %
 constexpr uint32_t kMaxBlock = 512;
 constexpr uint32_t kMaxWarps = kMaxBlock / 32;
 constexpr uint32_t kTaskLen = 64;     // adjacency entries per grid task
-constexpr uint32_t kCursorMin = 16;   // rows longer than this keep a window cursor
 // Round-phase shapes (pull prefix entries a lane answers itself, window
 // entries a lane relaxes at a time), per kernel: more of each is faster while
 // registers last; the batch and serving kernels hold more state.
@@ -452,8 +451,8 @@ __device__ void round_phase(const KArgs& A, const RoundCtx& R, const Local& L, R
   WarpList Qw = {T.wq[warp], 0u, R.qcnt_out, R.qout};
   WarpList Fw = {T.wf[warp], 0u, R.first_cnt, R.first_list};
   // An item's record: {vertex, dist, row begin, row end} for a frontier
-  // vertex or the source, {dist, row begin, row end} for the push set (from
-  // the settled list), the nz entry for a listed pull. Records are loaded one
+  // vertex or the source, {dist, row begin, row end, cursor} for the push set
+  // (from the settled list), the nz entry for a listed pull. Records are loaded one
   // warp iteration ahead, a frontier vertex's queue entry two ahead.
   // (the push set's settled-list vertices come in the same way, two ahead)
   auto fetch_id = [&](uint32_t ii) -> uint32_t {
@@ -467,7 +466,9 @@ __device__ void round_phase(const KArgs& A, const RoundCtx& R, const Local& L, R
       const uint32_t u = round1 ? L.s_int : id;
       return make_uint4(u, __ldcg(&A.dist[u]), __ldg(&A.G.row[u]), __ldg(&A.G.row[u + 1]));
     }
-    if (ii < np) return make_uint4(ld_list(&A.sd[L.push_beg + ii]), __ldg(&A.G.row[id]), __ldg(&A.G.row[id + 1]), 0u);
+    if (ii < np)
+      return make_uint4(ld_list(&A.sd[L.push_beg + ii]), __ldg(&A.G.row[id]), __ldg(&A.G.row[id + 1]),
+                        ld_list(&A.scur[L.push_beg + ii]));
     return ld_stream4(&A.G.nz[ii - np]);
   };
   // one warp iteration: each lane's item (kind kKindNone: no item)
@@ -499,7 +500,7 @@ __device__ void round_phase(const KArgs& A, const RoundCtx& R, const Local& L, R
           const uint32_t rb = rec.y, re = rec.z;
           if (!(d > 0 && re - rb == 1)) {
             C.frontier += 1;
-            const uint32_t cur = ld_list(&A.scur[idx]);
+            const uint32_t cur = rec.w;
             // windows of consecutive steps are contiguous: resume at the cursor
             b = cur == kNone ? lower_bound_w(A.G.adj, rb, re, R.lb - (int64_t)d)
                              : gallop_w(A.G.adj, rb + cur, re, R.lb - (int64_t)d);
@@ -1558,7 +1559,7 @@ __device__ void run_query(const KArgs& A, QueryShared& Q, uint32_t& gen) {
       for (uint32_t base = lbeg + qb * blockDim.x; base < lend; base += nthreads) {
         const uint32_t idx = base + threadIdx.x;
         bool take = false;
-        uint32_t x = 0, d = 0, r = EIC_INF, dg = 0;
+        uint32_t x = 0, d = 0, r = EIC_INF, dg = 0, cx = kNone;
         uint32_t xcur = 0;
         if constexpr (kRelaxIlp >= 2) {
           xcur = xnext;
@@ -1570,6 +1571,7 @@ __device__ void run_query(const KArgs& A, QueryShared& Q, uint32_t& gen) {
           else
             x = ld_list(&list[idx]);
           d = __ldcg(&A.dist[x]);
+          cx = x < A.G.nlong ? __ldcg(&A.cursor[x]) : kNone;  // (a long row by its id: loaded with dist)
           r = degree_rank(A.G, x);  // (the degree from the id: no random row read)
           dg = __ldg(&A.G.dvals[r]);
           take = true;
@@ -1590,7 +1592,7 @@ __device__ void run_query(const KArgs& A, QueryShared& Q, uint32_t& gen) {
           atomicOr(&A.sbits[x >> 5], 1u << (x & 31));
           if (!step1) {
             __stcg(&A.sd[idx], d);
-            __stcg(&A.scur[idx], dg > kCursorMin ? __ldcg(&A.cursor[x]) : kNone);
+            __stcg(&A.scur[idx], cx);
           }
           bdeg += dg;
           bmax = d > bmax ? d : bmax;
