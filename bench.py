@@ -74,7 +74,8 @@ def dist_env():
 # for the kernel code it was taken on: the key hashes the kernel sources without
 # their comments and blank lines, and any change to the code reports null.
 KERNEL_SOURCES = ("paper_2506_19349_gb300/csrc/sssp.cu", "paper_2506_19349_gb300/csrc/common.cuh",
-                  "paper_2506_19349_gb300/csrc/graph.h", "paper_2506_19349_gb300/csrc/stats.cuh", "include/eic.h")
+                  "paper_2506_19349_gb300/csrc/graph.h", "paper_2506_19349_gb300/csrc/graph.cu",
+                  "paper_2506_19349_gb300/csrc/stats.cuh", "include/eic.h")
 MEASURED_TRAFFIC = {  # {(scale, kernel code sha256): bytes per launch}
     (25, "1078127eac2b377d4f1f974a8121df4850d843f371bf184d62c8713303211ee2"): 6085168832,
 }
