@@ -77,7 +77,7 @@ KERNEL_SOURCES = ("paper_2506_19349_gb300/csrc/sssp.cu", "paper_2506_19349_gb300
                   "paper_2506_19349_gb300/csrc/graph.h", "paper_2506_19349_gb300/csrc/graph.cu",
                   "paper_2506_19349_gb300/csrc/stats.cuh", "include/eic.h")
 MEASURED_TRAFFIC = {  # {(scale, kernel code sha256): bytes per launch}
-    (25, "1078127eac2b377d4f1f974a8121df4850d843f371bf184d62c8713303211ee2"): 6085168832,
+    (25, "7196dabe0140fba2cc7cc789f776293ed5fff44287894c1d550bac8c4c4615e2"): 6090699648,
 }
 
 
