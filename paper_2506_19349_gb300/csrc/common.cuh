@@ -121,7 +121,18 @@ __device__ __forceinline__ void st_release_u32(uint32_t* p, uint32_t v) {
 struct GridBarrier {
   uint32_t count;
   uint32_t gen;
+  unsigned long long arrived;  // arrivals since the query started (single-query launches)
 };
+
+__device__ __forceinline__ void red_release_add_u64(unsigned long long* p, unsigned long long v) {
+  asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+__device__ __forceinline__ unsigned long long ld_acquire_gpu_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
 
 // Software barrier over nblocks co-resident (cooperatively launched) blocks:
 // the whole grid, or one block group of it. Every wait is bounded: after
@@ -153,6 +164,35 @@ __device__ __forceinline__ bool grid_barrier(GridBarrier* bar, uint32_t* gen_loc
       }
     }
     *gen_local = g + 1;
+    s_ok = ld_volatile_int(status) == 0;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+// The same barrier for a launch that runs one query. The arrival count only
+// grows while the query runs (its initialisation zeroes it), so a block
+// arrives with one release add that returns nothing and waits, with acquire
+// loads, until the count reaches its own next multiple of nblocks: no block
+// has to see the last arrival and publish a new generation. ticket: the
+// block's barriers passed so far times nblocks.
+__device__ __forceinline__ bool grid_barrier(GridBarrier* bar, unsigned long long* ticket, uint32_t nblocks,
+                                             uint64_t max_spin, int* status) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned long long target = *ticket + nblocks;
+    red_release_add_u64(&bar->arrived, 1ull);
+    uint64_t spins = 0;
+    while (ld_acquire_gpu_u64(&bar->arrived) < target) {
+      if (ld_volatile_int(status) != 0) break;
+      if (++spins > max_spin) {
+        atomicCAS(status, 0, EIC_ETIMEOUT);
+        break;
+      }
+      __nanosleep(64);
+    }
+    *ticket = target;
     s_ok = ld_volatile_int(status) == 0;
   }
   __syncthreads();

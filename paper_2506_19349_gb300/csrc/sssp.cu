@@ -1413,10 +1413,11 @@ struct QueryShared {
 
 // The query loop of Algorithm 1 run by the A.nb blocks of one query: rounds
 // of a step (item phase, task phase), statistics pass, step boundary, until
-// termination. gen is the block's copy of the barrier generation.
+// termination. gen is the block's copy of the barrier generation (uint32_t),
+// or its arrival ticket in a launch that runs this one query only (64-bit).
 // kFuse: 0 no fused rounds, 1 fused rounds, 2 as A.fuse says (per query).
-template <uint32_t kPullFast, uint32_t kRelaxIlp, uint32_t kFuse = 0>
-__device__ void run_query(const KArgs& A, QueryShared& Q, uint32_t& gen) {
+template <uint32_t kPullFast, uint32_t kRelaxIlp, uint32_t kFuse = 0, class Gen = uint32_t>
+__device__ void run_query(const KArgs& A, QueryShared& Q, Gen& gen) {
   PhaseScr& P = Q.P;
   Stage& T = Q.T;
   BState& B = Q.B;
@@ -1687,8 +1688,8 @@ __device__ void run_query(const KArgs& A, QueryShared& Q, uint32_t& gen) {
 
 __global__ void __launch_bounds__(kMaxBlock, 2) k_eic(KArgs A) {
   __shared__ QueryShared Q;
-  uint32_t gen = __ldcg(&A.ctl->bar.gen);
-  run_query<kPullFastSingle, kRelaxIlpSingle>(A, Q, gen);
+  unsigned long long ticket = 0;  // (k_init zeroed the arrival count)
+  run_query<kPullFastSingle, kRelaxIlpSingle>(A, Q, ticket);
 }
 
 // The same query with fused rounds (bucket fusion), for graphs whose every
@@ -1696,8 +1697,8 @@ __global__ void __launch_bounds__(kMaxBlock, 2) k_eic(KArgs A) {
 // rounds.
 __global__ void __launch_bounds__(kMaxBlock, 2) k_eic_fused(KArgs A) {
   __shared__ QueryShared Q;
-  uint32_t gen = __ldcg(&A.ctl->bar.gen);
-  run_query<kPullFastSingle, kRelaxIlpSingle, 1>(A, Q, gen);
+  unsigned long long ticket = 0;  // (k_init zeroed the arrival count)
+  run_query<kPullFastSingle, kRelaxIlpSingle, 1>(A, Q, ticket);
 }
 
 // Control block of a new query (one thread): the source's distance, the
@@ -1755,6 +1756,7 @@ __global__ void k_init(KArgs A) {
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     ctl_init(A);
     A.ctl->bar.count = 0;
+    A.ctl->bar.arrived = 0;
     A.ctl->status = 0;
   }
 }
